@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the SPIDER stencil path on GB300: GStencil/s.
+
+One benchmark "step" is one complete spider_run of the workload: every time
+step of it (e.g. 100 steps of a 7x7 box stencil on an 8192^2 grid), with the
+input grid resident in HBM.  GStencil/s = grid points x time steps / seconds
+/ 1e9.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d]
+                  [--precision tf32|f16x2|bf16x3] [--impl spider|reference] [--accuracy]
+
+Under torchrun every rank runs the whole workload on its own GPU (independent
+replicas, weak scaling); the reported value is the total over ranks divided
+by the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import stencil_inputs as si  # noqa: E402
+
+WORKLOADS = {
+    "box2d": si.BOX2D_R3_8192,
+    "heat2d": si.HEAT2D_512,
+    "heat3d": si.HEAT3D_512,
+    "box3d": si.BOX3D_512,
+}
+DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60}
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="spider", choices=["spider", "reference"])
+    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
+    ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="also compute the full-size relative L2 error against the FP64 oracle")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = DEFAULT_STEPS[a.workload]
+    a.warmup = max(3, a.warmup)
+    return a
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2506_22035_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (profiles/traffic.md rows:
+    | key | bytes per launch | source sha | ...)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha()
+    for line in open(path):
+        m = re.match(r"\|\s*([^|]+?)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|", line)
+        if m and m.group(1) == kernel_key and m.group(3) == sha:
+            return float(m.group(2))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded
+    sample of the workload (a crop of the grid, fewer time steps)."""
+    import oracle
+    u0, w = si.workload_inputs(wl, extents=tuple(min(e, 1024) for e in wl.extents) if wl.ndim == 2
+                               else tuple(min(e, 128) for e in wl.extents))
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.stencil(u0, w, 1)
+    one = max(time.perf_counter() - t0, 1e-4)
+    steps = int(max(1, min(wl.steps, budget_s / one)))
+    t0 = time.perf_counter()
+    oracle.stencil(u0, w, steps)
+    dt = time.perf_counter() - t0
+    pts = int(np.prod(u0.shape))
+    return {"value": pts * steps / dt / 1e9, "unit": "GStencil/s", "cores": cores, "kind": "oracle",
+            "sample": f"{wl.name} cropped to {'x'.join(map(str, u0.shape))}, {steps} time steps, FP64 direct "
+                      f"stencil (C, OpenMP, {cores} threads), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = WORKLOADS[a.workload]
+    # each benchmark step is a bounded sample of the workload, sized so the
+    # whole run (warm-up + timed) ends within about two minutes
+    per_step_budget = 90.0 / (a.steps + a.warmup)
+    side = 1024 if wl.ndim == 2 else 96
+    u0, w = si.workload_inputs(wl, extents=tuple(min(e, side) for e in wl.extents))
+    t0 = time.perf_counter()
+    oracle.stencil(u0, w, 1)
+    one = max(time.perf_counter() - t0, 1e-5)
+    while one > per_step_budget and min(u0.shape) > 16:
+        u0 = u0[tuple(slice(0, max(16, s // 2)) for s in u0.shape)].copy()
+        t0 = time.perf_counter()
+        oracle.stencil(u0, w, 1)
+        one = max(time.perf_counter() - t0, 1e-5)
+    tsteps = int(max(1, min(wl.steps, per_step_budget / one)))
+    for _ in range(a.warmup):
+        oracle.stencil(u0, w, tsteps)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.stencil(u0, w, tsteps)
+    dt = time.perf_counter() - t0
+    pts = int(np.prod(u0.shape))
+    value = pts * tsteps * a.steps / dt / 1e9
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": "GStencil/s", "value": value, "unit": "GStencil/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, a, extra={"sample": "x".join(map(str, u0.shape)), "time_steps": tsteps}),
+        "cpu_baseline": {"value": value, "unit": "GStencil/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{wl.name} cropped to {'x'.join(map(str, u0.shape))}, {tsteps} time steps per "
+                                   f"benchmark step"},
+        "e2e": {"value": value, "unit": "GStencil/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(wl, a, extra=None):
+    cfg = {"workload": f"{wl.name}, {wl.steps} time steps", "stencil": f"{wl.shape} r={wl.r} {wl.ndim}-D",
+           "extents": list(wl.extents), "time_steps": wl.steps, "precision": a.precision, "engine": a.engine,
+           "steps_per_pass": 1, "global_batch": 1,
+           "l2": "inputs larger than L2" if 4 * int(np.prod(wl.extents)) > L2_BYTES else "L2 flushed between timed runs",
+           "parallelism": f"replicas{a.gpus}"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ spider arm
+def time_runs(plan, a_in, b_out, steps_per_run, iters, flush_buf, stream):
+    """Total device seconds of `iters` runs (CUDA events on `stream`)."""
+    import torch
+    if flush_buf is None:
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(iters):
+            plan.run(a_in, b_out, steps_per_run, stream)
+        e.record(stream)
+        e.synchronize()
+        return s.elapsed_time(e) * 1e-3
+    total = 0.0
+    for _ in range(iters):
+        flush_buf.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        plan.run(a_in, b_out, steps_per_run, stream)
+        e.record(stream)
+        e.synchronize()
+        total += s.elapsed_time(e) * 1e-3
+    return total
+
+
+def run_spider(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2506_22035_gb300 as spider
+    from paper_2506_22035_gb300 import build as _b
+    _b.build()
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = WORKLOADS[a.workload]
+    u0, w = si.workload_inputs(wl)
+    pts = int(np.prod(wl.extents))
+    grid_bytes = 4 * pts
+    plan = spider.Plan(w, wl.extents, wl.shape, a.precision, a.engine)
+    a_in = torch.from_numpy(u0).to(dev)
+    b_out = torch.empty_like(a_in)
+    flush = None if grid_bytes > L2_BYTES else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(a.warmup):
+        plan.run(a_in, b_out, wl.steps, stream)
+    plan.sync(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    smi_index = visible[local] if local < len(visible) and visible[local].strip().isdigit() else str(local)
+    with ClockSampler(smi_index) as clk:
+        barrier()
+        dt = time_runs(plan, a_in, b_out, wl.steps, a.steps, flush, stream)
+        barrier()
+    plan.sync(stream)
+    if world > 1:
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    launches_per_run = wl.steps  # one launch per time step (steps_per_pass = 1)
+    total_launches = a.steps * launches_per_run
+    value = world * pts * wl.steps * a.steps / dt / 1e9
+    per_launch_s = dt / total_launches
+
+    result = None
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        alg_bytes = 8.0 * pts  # read every point once and write it once per step
+        achieved = alg_bytes / per_launch_s / 1e9
+        kernel_key = f"stencil_step_kernel {wl.name} {a.engine} {a.precision}"
+        traffic = traffic_from_profiles(kernel_key)
+        result = {
+            "metric": "GStencil/s", "value": value, "unit": "GStencil/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
+            "config": workload_config(wl, a),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "algorithmic_bytes_per_launch": alg_bytes, "launch_us": per_launch_s * 1e6},
+            "gpu_launches": total_launches,
+            "clocks": clk.summary(),
+        }
+
+    # end-to-end through the host-buffer entry point: pinned host input, H2D,
+    # all time steps, D2H, inside the timed region
+    host_in = torch.from_numpy(u0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    hin, hout = host_in.numpy(), host_out.numpy()
+    plan.run_host(hin, wl.steps, hout, stream)
+    e2e_iters = max(3, min(20, a.steps // 20))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        plan.run_host(hin, wl.steps, hout, stream)
+    e2e_dt = time.perf_counter() - t0
+    barrier()
+    if rank == 0:
+        result["e2e"] = {"value": world * pts * wl.steps * e2e_iters / e2e_dt / 1e9, "unit": "GStencil/s",
+                         "h2d_bytes_per_step": grid_bytes, "d2h_bytes_per_step": grid_bytes,
+                         "entry_point": "spider_run_host"}
+        ref_ok = np.isfinite(hout).all()
+        result["e2e"]["finite"] = bool(ref_ok)
+
+    # comparators and other precisions on the same GPU and workload
+    if rank == 0 and not a.no_comparators:
+        comps = {}
+        variants = [("sparse_tc", "tf32"), ("sparse_tc", "f16x2"), ("sparse_tc", "bf16x3"), ("dense_tc", "tf32"),
+                    ("cuda_core", "tf32")]
+        for eng, prec in variants:
+            if (eng, prec) == (a.engine, a.precision):
+                continue
+            p2 = spider.Plan(w, wl.extents, wl.shape, prec, eng)
+            iters = max(3, a.steps // 10)
+            for _ in range(2):
+                p2.run(a_in, b_out, wl.steps, stream)
+            torch.cuda.synchronize(dev)
+            d2 = time_runs(p2, a_in, b_out, wl.steps, iters, flush, stream)
+            p2.sync(stream)
+            comps[f"{eng}/{prec}"] = pts * wl.steps * iters / d2 / 1e9
+            p2.close()
+        result["comparators"] = comps
+
+    if rank == 0 and a.accuracy:
+        import oracle
+        ref = oracle.stencil(u0, w, wl.steps)
+        ref_t = torch.from_numpy(ref).to(dev)
+        errs = {}
+        for prec in ("tf32", "f16x2", "bf16x3"):
+            p2 = spider.Plan(w, wl.extents, wl.shape, prec)
+            p2.run(a_in, b_out, wl.steps, stream)
+            errs[prec] = spider.relative_l2_error(b_out, ref_t, stream)
+            p2.close()
+        result["rel_l2_error_vs_fp64"] = errs
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl)
+
+    plan.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_spider(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * spider.h -- C ABI of the GB300 (sm_103a) SPIDER stencil library.
+ *
+ * SPIDER (Sparse Tensor Cores for stencils via strided swapping) computes the
+ * stencil sweep
+ *
+ *     u_{t+1}[i] = sum_{o in S} w[o] * u_t[i + o]            (Sec. 1, Sec. 2.2)
+ *
+ * by lowering every kernel row to a banded matrix product Y = K X
+ * (Sec. 3.1.1), permuting K's columns ahead of time so that it has the 2:4
+ * (and 1:2) structured-sparse form Sparse Tensor Cores accept (Sec. 3.1.2),
+ * and applying the matching row permutation to the input while it is moved
+ * from shared memory to registers (Sec. 3.2).  The result is the same
+ * stencil; only rounding differs.
+ *
+ * Conventions for every entry point:
+ *  - Grids are float32, C-contiguous, x (last extent) fastest.  Outside the
+ *    grid the field is 0 at every step (zero Dirichlet halo); every point of
+ *    the grid is updated.
+ *  - Device pointers are CUDA device (or managed) memory of the current
+ *    device; the library never frees memory it does not own.  A plan owns its
+ *    packed operands and one scratch grid (allocated on first use).
+ *  - Calls that take a stream are asynchronous on that stream.  A status of
+ *    SPIDER_OK means the work was enqueued; faults detected by the device
+ *    (e.g. a wait that ran out) are reported by the next call on that plan
+ *    or by spider_plan_sync.
+ *  - No C++ exception crosses this boundary.  On error the call returns a
+ *    status other than SPIDER_OK, touches neither the device nor the outputs,
+ *    and spider_last_error() returns a message (thread-local).
+ */
+#ifndef SPIDER_H_
+#define SPIDER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spider_plan_t* spider_plan;
+typedef struct spider_server_t* spider_server;
+
+typedef enum {
+  SPIDER_OK = 0,
+  SPIDER_ERR_INVALID = 1,      /* bad argument; nothing was done              */
+  SPIDER_ERR_UNSUPPORTED = 2,  /* valid stencil outside what is built         */
+  SPIDER_ERR_OOM = 3,          /* device allocation or admission budget       */
+  SPIDER_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed           */
+  SPIDER_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out          */
+  SPIDER_ERR_BUSY = 6          /* server queue full; retry later              */
+} spider_status;
+
+typedef enum { SPIDER_STAR = 0, SPIDER_BOX = 1 } spider_shape;
+
+/* Arithmetic of the tensor-core products (accumulation is always FP32).
+ *  TF32   : one sparse TF32 product per kernel row (grid and weights rounded
+ *           to nearest TF32).
+ *  F16X2  : grid and weights split into FP16 hi + lo parts (lo parts scaled by
+ *           2^11); hi*hi + hi*lo + lo*hi.  Requires |grid values| < 32768.
+ *  BF16X3 : grid and weights split into BF16 hi + lo parts; the three
+ *           products hi*hi + hi*lo + lo*hi, FP32 range (no scaling).
+ *  AUTO   : TF32. */
+typedef enum { SPIDER_TF32 = 0, SPIDER_F16X2 = 1, SPIDER_BF16X3 = 2, SPIDER_AUTO = 3 } spider_precision;
+
+/* Which kernel a plan runs.  SPARSE_TC is SPIDER; the other two are the
+ * comparators built on the same tiling: DENSE_TC multiplies the same banded
+ * K without the 2:4 compression on dense tensor cores (the paper's "SPIDER w.
+ * TC" ablation, Sec. 4.4), CUDA_CORE is a direct FP32 FMA stencil. */
+typedef enum { SPIDER_ENGINE_SPARSE_TC = 0, SPIDER_ENGINE_DENSE_TC = 1, SPIDER_ENGINE_CUDA_CORE = 2 } spider_engine;
+
+/* spider_plan_create -- the paper's offline transform (Sec. 3.1, Sec. 3.3.2).
+ *
+ * Builds, for every kernel row of the stencil (Sec. 3.1.1), the banded matrix
+ * K (L = 8 outputs, a 16-wide input window), applies the strided column swap
+ * that gives the 2:4 / 1:2 pattern (Sec. 3.1.2), compresses it to values plus
+ * 2-bit metadata, and packs values and metadata per thread in fragment order
+ * (Sec. 3.3.2).  Host work only: no device is touched until the first run.
+ *
+ *  ndim      1, 2 or 3.
+ *  extents   ndim sizes, slowest axis first, x last; each >= 1; the product
+ *            must be < 2^40.
+ *  shape     SPIDER_STAR: only on-axis coefficients may be non-zero;
+ *            SPIDER_BOX: any.
+ *  radius    1..3.
+ *  coeffs    dense (2r+1)^ndim float32 cube, row-major [dz][dy][dx], each
+ *            offset running -r..r; host memory, copied; finite values only.
+ *  prec      see spider_precision.
+ *  out       receives the plan (owned by the caller; free with
+ *            spider_plan_destroy).
+ * Errors: SPIDER_ERR_INVALID (bad ndim/extents/radius/NULL, non-finite
+ * coefficients, non-zero off-axis coefficient for a star),
+ * SPIDER_ERR_UNSUPPORTED (radius > 3). */
+spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape shape, int radius,
+                                 const float* coeffs, spider_precision prec, spider_plan* out);
+
+/* Selects the kernel the plan runs (default SPIDER_ENGINE_SPARSE_TC).  The
+ * comparators support SPIDER_TF32 (DENSE_TC) and plain FP32 (CUDA_CORE,
+ * precision ignored). */
+spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
+
+/* Time steps fused per pass over HBM (1 = one launch per step).  Values the
+ * build does not support for the plan's stencil return SPIDER_ERR_UNSUPPORTED. */
+spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);
+
+/* Reads back the plan's packed operands (host copies) for inspection and
+ * testing.  Any pointer may be NULL; sizes are in 32-bit words.
+ *   n_operand_words / operand_words : tensor-core A fragments, per
+ *       [split term][kernel row][lane][4] words
+ *   n_meta_words / meta_words       : metadata, per [kernel row][lane]
+ * Returns SPIDER_ERR_INVALID if a buffer is given with a too small capacity. */
+spider_status spider_plan_operands(spider_plan plan, uint32_t* operand_words, size_t operand_capacity,
+                                   size_t* n_operand_words, uint32_t* meta_words, size_t meta_capacity,
+                                   size_t* n_meta_words);
+
+/* spider_run -- advances a grid by `steps` time steps (Sec. 3.2, Sec. 3.3.1).
+ *
+ *  grid_in   device, the plan's extents; read only (preserved).
+ *  grid_out  device, same size; must not overlap grid_in.  Receives the field
+ *            after `steps` steps; for steps == 0 it receives a copy of grid_in.
+ *  steps     >= 0.
+ *  stream    CUDA stream (0 = legacy default stream).
+ * The library ping-pongs between grid_out and a plan-owned scratch grid, so
+ * any step count ends in grid_out.  Calls on one plan must not overlap on the
+ * GPU (the scratch grid is shared); use one plan per concurrent stream. */
+spider_status spider_run(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
+                         cudaStream_t stream);
+
+/* spider_run_host -- spider_run for host buffers: copies host_in to a
+ * plan-owned device grid, runs, copies the result to host_out, and waits for
+ * completion.  host_in / host_out may be pageable or pinned host memory and
+ * may be the same buffer. */
+spider_status spider_run_host(spider_plan plan, const float* host_in, float* host_out, int64_t steps,
+                              cudaStream_t stream);
+
+/* Blocks until the plan's work on `stream` is done and reports any
+ * device-side error (SPIDER_ERR_TIMEOUT for an expired wait). */
+spider_status spider_plan_sync(spider_plan plan, cudaStream_t stream);
+
+void spider_plan_destroy(spider_plan plan);
+
+/* spider_batch -- advances n independent grids in one persistent launch.
+ * plans[i], ins[i], outs[i], steps[i] as for spider_run; every plan must be
+ * SPARSE_TC.  Work items (grid, tile, step) are taken from a device queue;
+ * step t+1 of a grid starts on a tile only after step t finished on the
+ * neighbouring tiles (per-grid counters with bounded waits).  n <= 4096. */
+spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
+                           const int64_t* steps, cudaStream_t stream);
+
+/* GPU FP64 validation reductions (the only FP64 the library runs on the GPU).
+ *   a    device float32 array of n values
+ *   ref  device float64 array of n values, or NULL
+ *   out  host double[4]: sum(a^2), sum(ref^2), sum((a-ref)^2), max|a-ref|
+ *        (the last two are 0 when ref is NULL).  Synchronous on `stream`. */
+spider_status spider_norms_fp64(const float* a, const double* ref, int64_t n, double* out, cudaStream_t stream);
+
+/* Constant-field invariant check: max |a[i] - value| over the points of a
+ * grid (extents as for plans) that lie farther than `margin` points from every
+ * face, computed in FP64 on the GPU.  Synchronous on `stream`. */
+spider_status spider_constant_check_fp64(const float* a, int ndim, const int64_t* extents, int64_t margin,
+                                         double value, double* max_dev, cudaStream_t stream);
+
+/* ---- serving: continuous batching of stencil jobs ---------------------------
+ * A server owns a worker thread and its own streams.  Jobs are admitted while
+ * their device memory (two grids) fits the HBM budget; jobs that arrive while
+ * others run are started as memory and slots free up, and their work overlaps
+ * on the device. */
+spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out);
+
+/* Submits a job.  `plan` is copied (the caller may destroy it afterwards).
+ * host_in: host grid of the plan's extents, copied before return.
+ * err_target: relative L2 error the caller accepts; <= 1e-4 selects a split
+ * precision, otherwise the plan's precision.  *ticket identifies the job.
+ * SPIDER_ERR_OOM if the job alone exceeds the budget; SPIDER_ERR_BUSY if the
+ * queue is full. */
+spider_status spider_submit(spider_server server, spider_plan plan, const float* host_in, int64_t steps,
+                            double err_target, uint64_t* ticket);
+
+/* Polls a job.  *done = 1 once finished; then, if out != NULL, the result is
+ * copied to host memory `out` and the job's record is released (a ticket can
+ * be read once).  latency_s (nullable) receives submit-to-completion seconds. */
+spider_status spider_poll(spider_server server, uint64_t ticket, float* out, int* done, double* latency_s);
+
+/* Stops the worker after the jobs already submitted finish, frees everything. */
+void spider_server_destroy(spider_server server);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* spider_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIDER_H_ */

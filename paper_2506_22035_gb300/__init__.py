@@ -1,0 +1,145 @@
+"""GB300-native SPIDER: stencils on Sparse Tensor Cores via strided swapping.
+
+The work is done by the CUDA library ``libspider.so`` (C ABI in
+``include/spider.h``); this package only marshals arguments to it.  Device
+memory and streams come from PyTorch tensors and streams.  There is no
+CPU fallback: calls fail when the library or a GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import (SPIDER_BF16X3, SPIDER_BOX, SPIDER_ENGINE_CUDA_CORE, SPIDER_ENGINE_DENSE_TC,
+                      SPIDER_ENGINE_SPARSE_TC, SPIDER_F16X2, SPIDER_STAR, SPIDER_TF32, SpiderError, check)
+
+PRECISIONS = {"tf32": SPIDER_TF32, "f16x2": SPIDER_F16X2, "bf16x3": SPIDER_BF16X3}
+ENGINES = {"sparse_tc": SPIDER_ENGINE_SPARSE_TC, "dense_tc": SPIDER_ENGINE_DENSE_TC,
+           "cuda_core": SPIDER_ENGINE_CUDA_CORE}
+SHAPES = {"star": SPIDER_STAR, "box": SPIDER_BOX}
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+class Plan:
+    """An owned ``spider_plan`` (see spider_plan_create)."""
+
+    def __init__(self, coeffs, extents, shape: str = "box", precision: str = "tf32", engine: str = "sparse_tc"):
+        lib = _native.load()
+        w = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
+        ext = tuple(int(e) for e in extents)
+        r = (w.shape[0] - 1) // 2
+        self.extents, self.radius, self.ndim = ext, r, len(ext)
+        self.shape_name, self.precision, self.engine = shape, precision, engine
+        handle = ctypes.c_void_p()
+        check(lib.spider_plan_create(len(ext), (ctypes.c_int64 * len(ext))(*ext), SHAPES[shape], r,
+                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), PRECISIONS[precision],
+                                     ctypes.byref(handle)), "spider_plan_create")
+        self._h = handle
+        if engine != "sparse_tc":
+            self.set_engine(engine)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def points(self) -> int:
+        return int(np.prod(self.extents))
+
+    def set_engine(self, engine: str) -> None:
+        check(_native.load().spider_plan_set_engine(self._h, ENGINES[engine]), "spider_plan_set_engine")
+        self.engine = engine
+
+    def set_steps_per_pass(self, t: int) -> None:
+        check(_native.load().spider_plan_set_steps_per_pass(self._h, int(t)), "spider_plan_set_steps_per_pass")
+
+    def operands(self):
+        lib = _native.load()
+        na, nm = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib.spider_plan_operands(self._h, None, 0, ctypes.byref(na), None, 0, ctypes.byref(nm)),
+              "spider_plan_operands")
+        a = np.zeros(na.value, dtype=np.uint32)
+        m = np.zeros(nm.value, dtype=np.uint32)
+        check(lib.spider_plan_operands(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), a.size, None,
+                                       m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), m.size, None),
+              "spider_plan_operands")
+        return a, m
+
+    def run(self, grid_in, grid_out, steps: int, stream=None) -> None:
+        """grid_in / grid_out: contiguous float32 CUDA tensors of the plan's extents."""
+        for t in (grid_in, grid_out):
+            if not t.is_cuda or not t.is_contiguous() or t.numel() != self.points:
+                raise ValueError("grids must be contiguous CUDA tensors of the plan's size")
+        check(_native.load().spider_run(self._h, _ptr(grid_in), _ptr(grid_out), int(steps), _stream_handle(stream)),
+              "spider_run")
+
+    def run_host(self, host_in: np.ndarray, steps: int, host_out: np.ndarray | None = None, stream=None):
+        src = np.ascontiguousarray(host_in, dtype=np.float32)
+        if src.size != self.points:
+            raise ValueError("host grid has the wrong size")
+        out = host_out if host_out is not None else np.empty_like(src)
+        check(_native.load().spider_run_host(self._h, src.ctypes.data_as(ctypes.c_void_p),
+                                             out.ctypes.data_as(ctypes.c_void_p), int(steps),
+                                             _stream_handle(stream)), "spider_run_host")
+        return out
+
+    def sync(self, stream=None) -> None:
+        check(_native.load().spider_plan_sync(self._h, _stream_handle(stream)), "spider_plan_sync")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _native.load().spider_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def norms_fp64(a, ref=None, stream=None):
+    """(sum a^2, sum ref^2, sum (a-ref)^2, max|a-ref|) computed in FP64 on the GPU."""
+    out = (ctypes.c_double * 4)()
+    check(_native.load().spider_norms_fp64(_ptr(a), _ptr(ref) if ref is not None else None, int(a.numel()), out,
+                                           _stream_handle(stream)), "spider_norms_fp64")
+    return tuple(out)
+
+
+def relative_l2_error(a, ref, stream=None) -> float:
+    _, srr, sdd, _ = norms_fp64(a, ref, stream)
+    return float(np.sqrt(sdd / srr)) if srr > 0 else float(np.sqrt(sdd))
+
+
+def constant_check_fp64(a, extents, margin: int, value: float, stream=None) -> float:
+    out = ctypes.c_double()
+    ext = tuple(int(e) for e in extents)
+    check(_native.load().spider_constant_check_fp64(_ptr(a), len(ext), (ctypes.c_int64 * len(ext))(*ext),
+                                                    int(margin), float(value), ctypes.byref(out),
+                                                    _stream_handle(stream)), "spider_constant_check_fp64")
+    return out.value
+
+
+def batch(plans, ins, outs, steps, stream=None) -> None:
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    I = (ctypes.c_void_p * n)(*[int(t.data_ptr()) for t in ins])
+    O = (ctypes.c_void_p * n)(*[int(t.data_ptr()) for t in outs])
+    S = (ctypes.c_int64 * n)(*[int(s) for s in steps])
+    check(_native.load().spider_batch(n, P, I, O, S, _stream_handle(stream)), "spider_batch")
+
+
+__all__ = ["Plan", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
+           "PRECISIONS", "ENGINES", "SHAPES"]

@@ -1,0 +1,298 @@
+// The C ABI (include/spider.h): plan lifecycle, spider_run, spider_run_host.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "launch.h"
+#include "spider_internal.h"
+
+namespace spider {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+spider_status fail(spider_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+static spider_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SPIDER_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SPIDER_CUDA(call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+static void free_device(spider_plan_t* p) {
+  DeviceState& d = p->dev;
+  if (d.device >= 0) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != d.device) cudaSetDevice(d.device);
+    cudaFree(d.a_words);
+    cudaFree(d.meta_words);
+    cudaFree(d.w_dense);
+    cudaFree(d.scratch);
+    cudaFree(d.host_stage_in);
+    cudaFree(d.host_stage_out);
+    cudaFree(d.status);
+    if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
+  }
+  d = DeviceState();
+}
+
+// Uploads the packed operands on first use (or after an engine change).
+static spider_status ensure_device(spider_plan_t* p) {
+  int dev = 0;
+  SPIDER_CUDA(cudaGetDevice(&dev));
+  DeviceState& d = p->dev;
+  if (d.device >= 0 && d.device != dev)
+    return fail(SPIDER_ERR_INVALID, "plan was first used on another device");
+  if (d.device < 0) d.device = dev;
+  if (!d.status) {
+    SPIDER_CUDA(cudaMalloc(&d.status, sizeof(int)));
+    SPIDER_CUDA(cudaMemset(d.status, 0, sizeof(int)));
+  }
+  if (!d.a_words && !p->a_words.empty()) {
+    SPIDER_CUDA(cudaMalloc(&d.a_words, p->a_words.size() * 4));
+    SPIDER_CUDA(cudaMemcpy(d.a_words, p->a_words.data(), p->a_words.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (!d.meta_words && !p->meta_words.empty()) {
+    SPIDER_CUDA(cudaMalloc(&d.meta_words, p->meta_words.size() * 4));
+    SPIDER_CUDA(cudaMemcpy(d.meta_words, p->meta_words.data(), p->meta_words.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (!d.w_dense) {
+    SPIDER_CUDA(cudaMalloc(&d.w_dense, p->w.size() * 4));
+    SPIDER_CUDA(cudaMemcpy(d.w_dense, p->w.data(), p->w.size() * 4, cudaMemcpyHostToDevice));
+  }
+  return SPIDER_OK;
+}
+
+static spider_status ensure_scratch(spider_plan_t* p) {
+  const size_t bytes = (size_t)p->points() * sizeof(float);
+  if (p->dev.scratch && p->dev.scratch_bytes >= bytes) return SPIDER_OK;
+  cudaFree(p->dev.scratch);
+  p->dev.scratch = nullptr;
+  cudaError_t e = cudaMalloc(&p->dev.scratch, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPIDER_ERR_OOM, std::string("scratch grid: ") + cudaGetErrorString(e));
+  }
+  p->dev.scratch_bytes = bytes;
+  return SPIDER_OK;
+}
+
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+// Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
+spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
+  const size_t bytes = (size_t)p->points() * sizeof(float);
+  if (steps == 0) {
+    SPIDER_CUDA(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, stream));
+    return SPIDER_OK;
+  }
+  spider_status s = ensure_device(p);
+  if (s != SPIDER_OK) return s;
+  if (steps > 1) {
+    s = ensure_scratch(p);
+    if (s != SPIDER_OK) return s;
+  }
+  LaunchCtx ctx;
+  ctx.plan = p;
+  ctx.stream = stream;
+  ctx.sms = device_sm_count();
+  // Ping-pong between out and the scratch grid; the parity of the first
+  // destination makes the last step land in out.
+  float* bufs[2] = {out, p->dev.scratch};
+  const int first = (steps % 2 == 1) ? 0 : 1;
+  for (int64_t t = 0; t < steps; ++t) {
+    ctx.dst = bufs[(first + t) % 2];
+    ctx.src = (t == 0) ? in : bufs[(first + t - 1) % 2];
+    cudaError_t e = launch_step(ctx);
+    if (e == cudaErrorNotSupported) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil/engine");
+    if (e != cudaSuccess) return cuda_fail(e, "stencil step launch");
+  }
+  return SPIDER_OK;
+}
+
+}  // namespace spider
+
+using namespace spider;
+
+extern "C" {
+
+const char* spider_last_error(void) { return spider::g_last_error.c_str(); }
+
+spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape shape, int radius,
+                                 const float* coeffs, spider_precision prec, spider_plan* out) {
+  set_error("");
+  if (!out) return fail(SPIDER_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3) return fail(SPIDER_ERR_INVALID, "ndim must be 1, 2 or 3");
+  if (!extents || !coeffs) return fail(SPIDER_ERR_INVALID, "extents/coeffs is NULL");
+  if (radius < 1) return fail(SPIDER_ERR_INVALID, "radius must be >= 1");
+  if (radius > kMaxR) return fail(SPIDER_ERR_UNSUPPORTED, "radius > 3 is not built");
+  if (shape != SPIDER_STAR && shape != SPIDER_BOX) return fail(SPIDER_ERR_INVALID, "bad shape");
+  if (prec < SPIDER_TF32 || prec > SPIDER_AUTO) return fail(SPIDER_ERR_INVALID, "bad precision");
+  long double total = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (extents[i] < 1) return fail(SPIDER_ERR_INVALID, "extents must be >= 1");
+    total *= (long double)extents[i];
+  }
+  if (total >= (long double)(1LL << 40)) return fail(SPIDER_ERR_INVALID, "grid too large");
+  const int side = 2 * radius + 1;
+  size_t ncoef = 1;
+  for (int i = 0; i < ndim; ++i) ncoef *= side;
+  for (size_t i = 0; i < ncoef; ++i) {
+    if (!std::isfinite(coeffs[i])) return fail(SPIDER_ERR_INVALID, "non-finite coefficient");
+    if (shape == SPIDER_STAR && coeffs[i] != 0.0f) {
+      // on-axis iff at most one offset differs from the centre
+      size_t rem = i;
+      int off_axis = 0;
+      for (int d = 0; d < ndim; ++d) {
+        if ((int)(rem % side) != radius) ++off_axis;
+        rem /= side;
+      }
+      if (off_axis > 1) return fail(SPIDER_ERR_INVALID, "star stencil with a non-zero off-axis coefficient");
+    }
+  }
+  spider_plan_t* p = new (std::nothrow) spider_plan_t();
+  if (!p) return fail(SPIDER_ERR_OOM, "host allocation");
+  p->ndim = ndim;
+  for (int i = 0; i < ndim; ++i) p->extents[i] = extents[i];
+  p->nx = extents[ndim - 1];
+  p->ny = ndim >= 2 ? extents[ndim - 2] : 1;
+  p->nz = ndim >= 3 ? extents[0] : 1;
+  p->shape = shape;
+  p->r = radius;
+  p->rx = radius;
+  p->ry = ndim >= 2 ? radius : 0;
+  p->rz = ndim >= 3 ? radius : 0;
+  p->prec = prec == SPIDER_AUTO ? SPIDER_TF32 : prec;
+  p->w.assign(coeffs, coeffs + ncoef);
+  spider_status s = build_operands(p);
+  if (s != SPIDER_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_CUDA_CORE) return fail(SPIDER_ERR_INVALID, "bad engine");
+  if (engine == SPIDER_ENGINE_DENSE_TC && p->prec != SPIDER_TF32)
+    return fail(SPIDER_ERR_UNSUPPORTED, "the dense tensor-core comparator runs TF32 only");
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (p->engine == engine) return SPIDER_OK;
+  p->engine = engine;
+  spider_status s = build_operands(p);
+  if (s != SPIDER_OK) return s;
+  // drop device copies of the old operands; they are uploaded again lazily
+  if (p->dev.device >= 0) {
+    cudaFree(p->dev.a_words);
+    cudaFree(p->dev.meta_words);
+    p->dev.a_words = nullptr;
+    p->dev.meta_words = nullptr;
+  }
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_set_steps_per_pass(spider_plan p, int steps_per_pass) {
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (steps_per_pass < 1) return fail(SPIDER_ERR_INVALID, "steps_per_pass must be >= 1");
+  if (steps_per_pass != 1) return fail(SPIDER_ERR_UNSUPPORTED, "temporal fusion is not built for this stencil");
+  p->steps_per_pass = steps_per_pass;
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_operands(spider_plan p, uint32_t* operand_words, size_t operand_capacity,
+                                   size_t* n_operand_words, uint32_t* meta_words, size_t meta_capacity,
+                                   size_t* n_meta_words) {
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (n_operand_words) *n_operand_words = p->a_words.size();
+  if (n_meta_words) *n_meta_words = p->meta_words.size();
+  if (operand_words) {
+    if (operand_capacity < p->a_words.size()) return fail(SPIDER_ERR_INVALID, "operand buffer too small");
+    std::memcpy(operand_words, p->a_words.data(), p->a_words.size() * 4);
+  }
+  if (meta_words) {
+    if (meta_capacity < p->meta_words.size()) return fail(SPIDER_ERR_INVALID, "metadata buffer too small");
+    std::memcpy(meta_words, p->meta_words.data(), p->meta_words.size() * 4);
+  }
+  return SPIDER_OK;
+}
+
+spider_status spider_run(spider_plan p, const float* grid_in, float* grid_out, int64_t steps, cudaStream_t stream) {
+  set_error("");
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (!grid_in || !grid_out) return fail(SPIDER_ERR_INVALID, "grid pointer is NULL");
+  if (steps < 0) return fail(SPIDER_ERR_INVALID, "steps must be >= 0");
+  if (overlaps(grid_in, grid_out, (size_t)p->points() * sizeof(float)))
+    return fail(SPIDER_ERR_INVALID, "grid_out overlaps grid_in");
+  std::lock_guard<std::mutex> lock(p->mu);
+  return run_device(p, grid_in, grid_out, steps, stream);
+}
+
+spider_status spider_run_host(spider_plan p, const float* host_in, float* host_out, int64_t steps,
+                              cudaStream_t stream) {
+  set_error("");
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (!host_in || !host_out) return fail(SPIDER_ERR_INVALID, "host pointer is NULL");
+  if (steps < 0) return fail(SPIDER_ERR_INVALID, "steps must be >= 0");
+  std::lock_guard<std::mutex> lock(p->mu);
+  spider_status s = ensure_device(p);
+  if (s != SPIDER_OK) return s;
+  const size_t bytes = (size_t)p->points() * sizeof(float);
+  if (!p->dev.host_stage_in) {
+    cudaError_t e = cudaMalloc(&p->dev.host_stage_in, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->dev.host_stage_out, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPIDER_ERR_OOM, "device grids for host run");
+    }
+  }
+  SPIDER_CUDA(cudaMemcpyAsync(p->dev.host_stage_in, host_in, bytes, cudaMemcpyHostToDevice, stream));
+  s = run_device(p, p->dev.host_stage_in, p->dev.host_stage_out, steps, stream);
+  if (s != SPIDER_OK) return s;
+  SPIDER_CUDA(cudaMemcpyAsync(host_out, p->dev.host_stage_out, bytes, cudaMemcpyDeviceToHost, stream));
+  SPIDER_CUDA(cudaStreamSynchronize(stream));
+  int status = 0;
+  SPIDER_CUDA(cudaMemcpy(&status, p->dev.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status != 0) return fail(SPIDER_ERR_TIMEOUT, "a device-side wait ran out");
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_sync(spider_plan p, cudaStream_t stream) {
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  SPIDER_CUDA(cudaStreamSynchronize(stream));
+  if (p->dev.status) {
+    int status = 0;
+    SPIDER_CUDA(cudaMemcpy(&status, p->dev.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+      cudaMemset(p->dev.status, 0, sizeof(int));
+      return fail(SPIDER_ERR_TIMEOUT, "a device-side wait ran out");
+    }
+  }
+  return SPIDER_OK;
+}
+
+void spider_plan_destroy(spider_plan p) {
+  if (!p) return;
+  free_device(p);
+  delete p;
+}
+
+}  // extern "C"

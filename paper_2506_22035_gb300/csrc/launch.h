@@ -1,0 +1,40 @@
+// Host-side launch of one stencil time step.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "spider_internal.h"
+
+namespace spider {
+
+struct LaunchCtx {
+  const spider_plan_t* plan;
+  const float* src;
+  float* dst;
+  cudaStream_t stream;
+  int sms;
+};
+
+// Launches one time step src -> dst for the plan's engine and precision.
+// Returns cudaSuccess, or the launch/tensor-map error.
+cudaError_t launch_step(const LaunchCtx& ctx);
+
+// Per-mode dispatchers (one translation unit each, compiled in parallel).
+// `cls` is 1, 2 or 3 (stencil dimensionality), r the radius.
+// Each returns cudaErrorNotSupported when it has no kernel for (cls, r).
+cudaError_t launch_sp_tf32(int cls, int r, const LaunchCtx& ctx);
+cudaError_t launch_sp_f16x2(int cls, int r, const LaunchCtx& ctx);
+cudaError_t launch_sp_bf16x3(int cls, int r, const LaunchCtx& ctx);
+cudaError_t launch_dense_tf32(int cls, int r, const LaunchCtx& ctx);
+cudaError_t launch_cuda_core(int cls, int r, const LaunchCtx& ctx);
+
+// Builds a 3-D tiled tensor map over a float32 grid (nz, ny, nx) with the
+// given box; out-of-range box elements read as zero.  Returns false if the
+// grid cannot be described (row pitch or base not 16-byte aligned).
+bool make_tensor_map(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int box_x, int box_y,
+                     int box_z);
+
+int device_sm_count();
+
+}  // namespace spider

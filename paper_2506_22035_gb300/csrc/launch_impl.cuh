@@ -1,0 +1,81 @@
+// Template launcher shared by the per-mode dispatch translation units.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "launch.h"
+#include "stencil_kernels.cuh"
+
+namespace spider {
+
+template <class C, Mode MODE>
+cudaError_t launch_cfg(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  auto kern = stencil_step_kernel<C, MODE>;
+  // Per-device one-time setup: opt into the dynamic shared memory and read
+  // the occupancy that sizes the persistent grid.
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
+  a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
+  a.tiles_z = (int)((p->nz + C::BZ - 1) / C::BZ);
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  a.use_tma = make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, C::SZ) ? 1 : 0;
+  const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z;
+  if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
+  kern<<<grid, C::kThreads, C::kSmemBytes, ctx.stream>>>(map, a);
+  return cudaGetLastError();
+}
+
+// Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
+// 3-D (planes x 16 x 128 outputs).
+template <int R, Mode MODE>
+cudaError_t launch_class(int cls, const LaunchCtx& ctx) {
+  if (cls == 1) return launch_cfg<TileCfg<0, 0, R, 1, 1, 2, 2>, MODE>(ctx);
+  if (cls == 2) return launch_cfg<TileCfg<0, R, R, 1, 4, 2, 16>, MODE>(ctx);
+  if (cls == 3) return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE>(ctx);
+  return cudaErrorNotSupported;
+}
+
+template <Mode MODE>
+cudaError_t launch_mode(int cls, int r, const LaunchCtx& ctx) {
+  switch (r) {
+    case 1: return launch_class<1, MODE>(cls, ctx);
+    case 2: return launch_class<2, MODE>(cls, ctx);
+    case 3: return launch_class<3, MODE>(cls, ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace spider

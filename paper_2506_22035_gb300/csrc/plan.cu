@@ -1,0 +1,284 @@
+// Host-side offline transform (Sec. 3.1) and operand packing (Sec. 3.3.2).
+//
+// For each dz plane and each A index a (see spider_internal.h) the 16 x 16
+// matrix A_a is assembled in window coordinates: row m = (s, xo) with
+// s = m / 8 the output row (y + s) and xo = m % 8 the output within the
+// segment; column p is window position p (input x = x0 - 4 + p).  Its entry
+// is w[dz][dy][dx] with dy = a - ry - s and dx = p - 4 - xo when both are in
+// range (the banded kernel matrix of Sec. 3.1.1 for kernel row dy, shifted to
+// the 16-wide window), else a structural zero.
+//
+// The MMA's K order is then taken through the strided permutation phi
+// (spider_internal.h), which puts the two members of every 1:2 pair / the
+// four members of every 2:4 group 8 window positions apart.  A band of
+// 2r+1 <= 7 consecutive positions can hold at most one member of a pair and
+// at most two of a group, so the permuted matrix is 1:2 and 2:4 structured
+// sparse (Sec. 3.1.2).  Compression keeps the band positions in their
+// original order with 2-bit indices, increasing, least significant bits
+// first; a group with fewer than two band positions is completed with a
+// zero placeholder at the next free index (Sec. 3.1.2, stage 3).
+//
+// Packing (Sec. 3.3.2): every lane's A registers of one MMA are contiguous
+// (one 16-byte load), consecutive MMAs follow each other, and the metadata
+// word of each lane is stored next to its neighbours, so the kernel fills its
+// registers with coalesced loads.
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "spider_internal.h"
+
+namespace spider {
+
+uint32_t round_tf32_rna(float x) {
+  // Round to the nearest value with a 10-bit mantissa, ties away from zero
+  // (the rounding of cvt.rna.tf32.f32): add half of the dropped range to the
+  // magnitude bits and clear the 13 low bits.  Inputs are finite.
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x1000u;
+  u &= 0xFFFFE000u;
+  return u;
+}
+
+float tf32_value(float x) {
+  uint32_t u = round_tf32_rna(x);
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+static uint16_t h_bits(float x) {
+  __half h = __float2half_rn(x);
+  uint16_t u;
+  std::memcpy(&u, &h, 2);
+  return u;
+}
+static float h_value(float x) { return __half2float(__float2half_rn(x)); }
+static uint16_t bf_bits(float x) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  uint16_t u;
+  std::memcpy(&u, &h, 2);
+  return u;
+}
+static float bf_value(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+int combos_per_plane(spider_precision prec, int ry) {
+  switch (prec) {
+    case SPIDER_F16X2:
+    case SPIDER_BF16X3:
+      return (ry + 1) + (2 * ry + 2);
+    default:
+      return 2 * ry + 2;
+  }
+}
+
+namespace {
+
+// Which part of a coefficient an operand carries.
+enum class Part { Full, TF32, F16Hi, F16LoScaled, BF16Hi, BF16Lo };
+
+float part_value(float w, Part part) {
+  switch (part) {
+    case Part::Full: return w;
+    case Part::TF32: return tf32_value(w);
+    case Part::F16Hi: return h_value(w);
+    case Part::F16LoScaled: return h_value((w - h_value(w)) * 2048.0f);
+    case Part::BF16Hi: return bf_value(w);
+    case Part::BF16Lo: return bf_value(w - bf_value(w));
+  }
+  return 0.f;
+}
+
+struct WindowMatrix {
+  float v[16][16];
+  bool mask[16][16];
+};
+
+// A_a for plane dz (index dzi = dz + rz) in window coordinates.
+WindowMatrix window_matrix(const spider_plan_t* p, int dzi, int a, Part part) {
+  WindowMatrix A;
+  const int wy = 2 * p->ry + 1, wx = 2 * p->rx + 1;
+  for (int m = 0; m < 16; ++m) {
+    const int s = m / 8, xo = m % 8;
+    const int dy = a - p->ry - s;
+    for (int q = 0; q < 16; ++q) {
+      const int dx = q - kHaloX - xo;
+      const bool in = (dy >= -p->ry && dy <= p->ry && dx >= -p->rx && dx <= p->rx);
+      A.mask[m][q] = in;
+      A.v[m][q] = in ? part_value(p->w[((size_t)dzi * wy + (dy + p->ry)) * wx + (dx + p->rx)], part) : 0.f;
+    }
+  }
+  return A;
+}
+
+uint32_t f32_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+}
+
+// TF32 m16n8k16, 1:2 on K pairs (2c, 2c+1).  Fragment maps (verified on the
+// device): A compressed 16 x 8 -- a0 (g, q), a1 (g+8, q), a2 (g, q+4),
+// a3 (g+8, q+4) with g = lane/4, q = lane%4; metadata (selector 0) -- lanes
+// with q in {0,1} hold row g pairs 4q..4q+3 in bits 0-15 and row g+8 in bits
+// 16-31, one nibble per pair: 0b0100 keeps the first element, 0b1110 the
+// second.
+void pack_tf32_sparse(const WindowMatrix& A, uint32_t* words /*32x4*/, uint32_t* meta /*32*/) {
+  float cval[16][8];
+  int cidx[16][8];
+  for (int m = 0; m < 16; ++m) {
+    for (int c = 0; c < 8; ++c) {
+      const int p0 = phi_tf32(2 * c), p1 = phi_tf32(2 * c + 1);
+      if (A.mask[m][p0] && A.mask[m][p1]) throw std::runtime_error("internal: pair not 1:2");
+      if (A.mask[m][p1]) { cidx[m][c] = 1; cval[m][c] = A.v[m][p1]; }
+      else { cidx[m][c] = 0; cval[m][c] = A.mask[m][p0] ? A.v[m][p0] : 0.f; }
+    }
+  }
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane / 4, q = lane % 4;
+    words[lane * 4 + 0] = f32_bits(cval[g][q]);
+    words[lane * 4 + 1] = f32_bits(cval[g + 8][q]);
+    words[lane * 4 + 2] = f32_bits(cval[g][q + 4]);
+    words[lane * 4 + 3] = f32_bits(cval[g + 8][q + 4]);
+    uint32_t e = 0;
+    if (q < 2) {
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t n0 = cidx[g][4 * q + i] ? 0xEu : 0x4u;
+        const uint32_t n1 = cidx[g + 8][4 * q + i] ? 0xEu : 0x4u;
+        e |= n0 << (4 * i);
+        e |= n1 << (16 + 4 * i);
+      }
+    }
+    meta[lane] = e;
+  }
+}
+
+// Dense TF32 m16n8k8, two K halves: a0 (g, q), a1 (g+8, q), a2 (g, q+4),
+// a3 (g+8, q+4) with column = K-index within the half.
+void pack_tf32_dense(const WindowMatrix& A, uint32_t* words /*32x8*/) {
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane / 4, q = lane % 4;
+    for (int h = 0; h < 2; ++h) {
+      auto val = [&](int row, int col) { return f32_bits(A.v[row][phi_tf32(8 * h + col)]); };
+      words[lane * 8 + 4 * h + 0] = val(g, q);
+      words[lane * 8 + 4 * h + 1] = val(g + 8, q);
+      words[lane * 8 + 4 * h + 2] = val(g, q + 4);
+      words[lane * 8 + 4 * h + 3] = val(g + 8, q + 4);
+    }
+  }
+}
+
+// Group compression of 4 K-indices with the placeholder rule.
+void compress_group(const bool in[4], int idx[2]) {
+  int n = 0, pos[4];
+  for (int j = 0; j < 4; ++j) if (in[j]) pos[n++] = j;
+  if (n > 2) throw std::runtime_error("internal: group not 2:4");
+  if (n == 2) { idx[0] = pos[0]; idx[1] = pos[1]; }
+  else if (n == 1) {
+    if (pos[0] < 3) { idx[0] = pos[0]; idx[1] = pos[0] + 1; }
+    else { idx[0] = 2; idx[1] = 3; }
+  } else { idx[0] = 0; idx[1] = 1; }
+}
+
+// 16-bit m16n8k32, 2:4.  K half 0 is window matrix H0, half 1 is H1.
+// Fragment maps (verified on the device): A compressed 16 x 16 --
+// a0 (g, 2q..2q+1), a1 (g+8, 2q..), a2 (g, 2q+8..), a3 (g+8, 2q+8..);
+// metadata (selector 0) -- lanes with q in {0,1}: nibble i = row g, group
+// 4q+i; nibble 4+i = row g+8, group 4q+i; nibble = idx0 | idx1 << 2.
+void pack_16bit_sparse_k32(const WindowMatrix& H0, const WindowMatrix& H1, bool bf16,
+                           uint32_t* words /*32x4*/, uint32_t* meta /*32*/) {
+  float cval[16][16];
+  int cidx[16][8][2];
+  for (int m = 0; m < 16; ++m) {
+    for (int c = 0; c < 8; ++c) {
+      const WindowMatrix& H = c < 4 ? H0 : H1;
+      const int c4 = c % 4;
+      bool in[4];
+      int pos[4];
+      for (int j = 0; j < 4; ++j) { pos[j] = phi_16bit(4 * c4 + j); in[j] = H.mask[m][pos[j]]; }
+      int idx[2];
+      compress_group(in, idx);
+      cidx[m][c][0] = idx[0];
+      cidx[m][c][1] = idx[1];
+      for (int s = 0; s < 2; ++s) cval[m][2 * c + s] = in[idx[s]] ? H.v[m][pos[idx[s]]] : 0.f;
+    }
+  }
+  auto bits = [&](float x) -> uint32_t { return bf16 ? bf_bits(x) : h_bits(x); };
+  auto pack2 = [&](int row, int col) { return bits(cval[row][col]) | (bits(cval[row][col + 1]) << 16); };
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane / 4, q = lane % 4;
+    words[lane * 4 + 0] = pack2(g, 2 * q);
+    words[lane * 4 + 1] = pack2(g + 8, 2 * q);
+    words[lane * 4 + 2] = pack2(g, 2 * q + 8);
+    words[lane * 4 + 3] = pack2(g + 8, 2 * q + 8);
+    uint32_t e = 0;
+    if (q < 2) {
+      for (int i = 0; i < 4; ++i) {
+        const int grp = 4 * q + i;
+        e |= (uint32_t)(cidx[g][grp][0] | (cidx[g][grp][1] << 2)) << (4 * i);
+        e |= (uint32_t)(cidx[g + 8][grp][0] | (cidx[g + 8][grp][1] << 2)) << (16 + 4 * i);
+      }
+    }
+    meta[lane] = e;
+  }
+}
+
+}  // namespace
+
+spider_status build_operands(spider_plan_t* p) {
+  const int planes = 2 * p->rz + 1;
+  const int na = 2 * p->ry + 2;
+  p->n_arows = planes * na;
+  p->a_words.clear();
+  p->meta_words.clear();
+  try {
+    if (p->engine == SPIDER_ENGINE_CUDA_CORE) {
+      p->n_combos = 0;
+      return SPIDER_OK;
+    }
+    if (p->engine == SPIDER_ENGINE_DENSE_TC) {
+      p->n_combos = p->n_arows;
+      p->a_words.resize((size_t)p->n_arows * 32 * 8);
+      for (int dzi = 0; dzi < planes; ++dzi)
+        for (int a = 0; a < na; ++a)
+          pack_tf32_dense(window_matrix(p, dzi, a, Part::TF32), &p->a_words[((size_t)dzi * na + a) * 256]);
+      return SPIDER_OK;
+    }
+    const int cpp = combos_per_plane(p->prec, p->ry);
+    p->n_combos = planes * cpp;
+    p->a_words.resize((size_t)p->n_combos * 128);
+    p->meta_words.resize((size_t)p->n_combos * 32);
+    for (int dzi = 0; dzi < planes; ++dzi) {
+      if (p->prec == SPIDER_TF32 || p->prec == SPIDER_AUTO) {
+        for (int a = 0; a < na; ++a) {
+          const size_t c = (size_t)dzi * cpp + a;
+          pack_tf32_sparse(window_matrix(p, dzi, a, Part::TF32), &p->a_words[c * 128], &p->meta_words[c * 32]);
+        }
+      } else {
+        const bool bf = p->prec == SPIDER_BF16X3;
+        const Part hi = bf ? Part::BF16Hi : Part::F16Hi;
+        const Part lo = bf ? Part::BF16Lo : Part::F16LoScaled;
+        // main combos: [K_hi(2c) | K_hi(2c+1)] times [X_hi(j); X_hi(j+1)]
+        for (int c = 0; c <= p->ry; ++c) {
+          const size_t ci = (size_t)dzi * cpp + c;
+          pack_16bit_sparse_k32(window_matrix(p, dzi, 2 * c, hi), window_matrix(p, dzi, 2 * c + 1, hi), bf,
+                                &p->a_words[ci * 128], &p->meta_words[ci * 32]);
+        }
+        // correction combos: [K_hi(a) | K_lo(a)] times [X_lo(j); X_hi(j)]
+        for (int a = 0; a < na; ++a) {
+          const size_t ci = (size_t)dzi * cpp + (p->ry + 1) + a;
+          pack_16bit_sparse_k32(window_matrix(p, dzi, a, hi), window_matrix(p, dzi, a, lo), bf,
+                                &p->a_words[ci * 128], &p->meta_words[ci * 32]);
+        }
+      }
+    }
+  } catch (const std::exception& e) {
+    return fail(SPIDER_ERR_INVALID, e.what());
+  }
+  return SPIDER_OK;
+}
+
+}  // namespace spider

@@ -1,0 +1,100 @@
+// Internal definitions shared by the host plan code and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <mutex>
+
+#include "spider.h"
+
+namespace spider {
+
+// ---------------------------------------------------------------- geometry
+// Every stencil is handled as 3-D (nz, ny, nx) with per-axis radii
+// (rz, ry, rx); a 2-D stencil has rz = 0 and nz = 1, a 1-D one also ry = 0.
+//
+// Tensor-core tile geometry (Sec. 3.1.1 with L = 8, Sec. 3.3.1):
+//  * a "segment" is L = 8 consecutive outputs along x; its input window is
+//    the 16 points x0-4 .. x0+11 (4 >= r points of halo on each side, which
+//    keeps every window start 16-byte aligned);
+//  * an MMA covers M = 16 rows = two vertically adjacent output rows (y, y+1)
+//    x 8 outputs of one segment, N = 8 segments, K = the 16-point window of
+//    one input row (z + dz, j).  The top half of A holds kernel row
+//    dy = j - y, the bottom half dy = j - y - 1, so one B fragment of input
+//    row j feeds both output rows and the accumulator never moves;
+//  * "A index" a = j - y + ry runs 0 .. 2ry+1 for each dz.
+constexpr int kSeg = 8;          // L: outputs per segment
+constexpr int kWin = 16;         // 2L: input window per segment
+constexpr int kHaloX = 4;        // window starts 4 points left of the segment
+constexpr int kMaxR = 3;
+
+// Fragment-aware strided permutation.  MMA K-index k of the TF32
+// m16n8k16 B fragment lives in lane q = k % 4, register i = k / 4; we place
+// it at window position phi(k) = 4*sigma(q) + i, so each lane's four B
+// values are four consecutive floats (one 16-byte shared-memory load), and
+// the 1:2 pairs (2c, 2c+1) land on window positions 8 apart -- the strided
+// swap of Sec. 3.1.2 with stride L = 8.  For FP16/BF16 m16n8k32 the same
+// sigma places K-index k' = 2q + 8s + h of each 16-wide half at
+// 4*sigma(q) + 2s + h, so 2:4 groups are {p, p+1, p+8, p+9}.
+constexpr int kSigma[4] = {0, 2, 1, 3};
+inline int phi_tf32(int k) { return 4 * kSigma[k % 4] + k / 4; }
+inline int phi_16bit(int kk) {  // kk in [0, 16) within one K half
+  int q = (kk % 8) / 2, s = kk / 8, h = kk % 2;
+  return 4 * kSigma[q] + 2 * s + h;
+}
+
+// -------------------------------------------------------------- the plan
+enum class Term : int { Single = 0 };
+
+struct DeviceState {
+  int device = -1;
+  uint32_t* a_words = nullptr;     // packed A fragments
+  uint32_t* meta_words = nullptr;  // packed metadata
+  float* w_dense = nullptr;        // dense coefficient cube (CUDA-core engine)
+  float* scratch = nullptr;        // ping-pong grid
+  float* host_stage_in = nullptr;  // device grids for spider_run_host
+  float* host_stage_out = nullptr;
+  int* status = nullptr;           // device error word (0 = ok)
+  size_t scratch_bytes = 0;
+};
+
+}  // namespace spider
+
+struct spider_plan_t {
+  int ndim = 0;
+  int64_t extents[3] = {1, 1, 1};
+  int64_t nz = 1, ny = 1, nx = 1;
+  spider_shape shape = SPIDER_BOX;
+  int r = 1, rz = 0, ry = 0, rx = 1;
+  spider_precision prec = SPIDER_TF32;
+  spider_engine engine = SPIDER_ENGINE_SPARSE_TC;
+  int steps_per_pass = 1;
+  std::vector<float> w;                  // (2rz+1)(2ry+1)(2rx+1), [dz][dy][dx]
+  // Packed operands, see plan.cpp for the layouts.
+  int n_arows = 0;                       // A matrices per split term = (2rz+1)(2ry+2)
+  int n_combos = 0;                      // A operands actually issued per dz-plane set
+  std::vector<uint32_t> a_words;         // [combo][lane][4]  (dense TF32: [arow][lane][8])
+  std::vector<uint32_t> meta_words;      // [combo][lane]
+  spider::DeviceState dev;
+  std::mutex mu;
+
+  int64_t points() const { return nz * ny * nx; }
+};
+
+namespace spider {
+
+// thread-local last-error message
+void set_error(const std::string& msg);
+spider_status fail(spider_status s, const std::string& msg);
+
+// plan.cpp
+spider_status build_operands(spider_plan_t* p);
+uint32_t round_tf32_rna(float x);
+float tf32_value(float x);
+
+// Number of A "combos" (register operands) for a precision, per dz plane.
+int combos_per_plane(spider_precision prec, int ry);
+
+}  // namespace spider

@@ -1,0 +1,210 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every entry point
+declared in include/spider.h, validates its arguments, and its host-side plan
+(the offline transform of Sec. 3.1 and the fragment packing of Sec. 3.3.2)
+packs operands that decode back to the stencil's banded kernel matrices.
+
+No compute call is made here (plan creation touches no device)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_22035_gb300 as spider
+from paper_2506_22035_gb300 import _native, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load()
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(spider_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert {"spider_plan_create", "spider_run", "spider_batch", "spider_submit"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding declares exactly the header's entry points
+    assert set(_native.SIGNATURES) == names
+
+
+def _create(lib, ndim, ext, shape, r, coeffs, prec=0):
+    h = ctypes.c_void_p()
+    w = np.ascontiguousarray(coeffs, dtype=np.float32)
+    st = lib.spider_plan_create(ndim, (ctypes.c_int64 * max(1, len(ext)))(*ext), shape, r,
+                                w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), prec, ctypes.byref(h))
+    if st == 0:
+        lib.spider_plan_destroy(h)
+    return st
+
+
+def test_plan_argument_validation(lib):
+    ok = np.ones((3, 3), np.float32)
+    assert _create(lib, 2, (16, 16), 1, 1, ok) == _native.SPIDER_OK
+    assert _create(lib, 4, (16, 16), 1, 1, ok) == _native.SPIDER_ERR_INVALID
+    assert _create(lib, 2, (0, 16), 1, 1, ok) == _native.SPIDER_ERR_INVALID
+    assert _create(lib, 2, (16, 16), 1, 0, ok) == _native.SPIDER_ERR_INVALID
+    assert _create(lib, 2, (16, 16), 1, 4, np.ones((9, 9), np.float32)) == _native.SPIDER_ERR_UNSUPPORTED
+    bad = ok.copy()
+    bad[0, 0] = np.nan
+    assert _create(lib, 2, (16, 16), 1, 1, bad) == _native.SPIDER_ERR_INVALID
+    # a star stencil may not carry off-axis coefficients
+    assert _create(lib, 2, (16, 16), 0, 1, ok) == _native.SPIDER_ERR_INVALID
+    star = np.zeros((3, 3), np.float32)
+    star[1, :] = 1
+    star[:, 1] = 1
+    assert _create(lib, 2, (16, 16), 0, 1, star) == _native.SPIDER_OK
+    assert lib.spider_plan_create(2, None, 1, 1, None, 0, None) == _native.SPIDER_ERR_INVALID
+    assert b"NULL" in lib.spider_last_error()
+
+
+def test_run_rejects_bad_arguments_without_touching_a_device(lib):
+    p = spider.Plan(np.ones((3, 3), np.float32), (8, 8))
+    assert lib.spider_run(p.handle, None, None, 1, None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_run(p.handle, ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 16), 1, None) == \
+        _native.SPIDER_ERR_INVALID                                   # overlapping grids
+    assert lib.spider_run(p.handle, ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), -1, None) == \
+        _native.SPIDER_ERR_INVALID
+    assert lib.spider_plan_set_steps_per_pass(p.handle, 0) == _native.SPIDER_ERR_INVALID
+    p.close()
+
+
+# ------------------------------------------------------------------ operand decoding
+# Decoding uses the fragment maps of the sparse TF32 m16n8k16 MMA (measured on
+# the device): A compressed 16 x 8 with a0 (g, q), a1 (g+8, q), a2 (g, q+4),
+# a3 (g+8, q+4); metadata in lanes q in {0,1}: nibble i of the low half is row
+# g, pair 4q+i, of the high half row g+8; 0x4 keeps the first element of the
+# pair, 0xE the second.  MMA K-index k sits at window position
+# 4*sigma(k % 4) + k // 4 with sigma = (0, 2, 1, 3).
+
+SIGMA = (0, 2, 1, 3)
+
+
+def phi(k):
+    return 4 * SIGMA[k % 4] + k // 4
+
+
+def decode_tf32(words, meta):
+    """16 x 16 window matrix from one A operand (words: 32 x 4, meta: 32)."""
+    comp = np.zeros((16, 8), np.float32)
+    idx = np.full((16, 8), -1)
+    for lane in range(32):
+        g, q = divmod(lane, 4)
+        vals = words[lane].view(np.float32)
+        comp[g, q], comp[g + 8, q], comp[g, q + 4], comp[g + 8, q + 4] = vals
+        if q < 2:
+            for i in range(4):
+                for half, row in ((0, g), (16, g + 8)):
+                    nib = (int(meta[lane]) >> (half + 4 * i)) & 0xF
+                    assert nib in (0x4, 0xE)
+                    idx[row, 4 * q + i] = 0 if nib == 0x4 else 1
+    assert (idx >= 0).all()
+    A = np.zeros((16, 16), np.float32)
+    for m in range(16):
+        for c in range(8):
+            A[m, phi(2 * c + idx[m, c])] += comp[m, c]
+    return A
+
+
+def expected_window(w, a, ry, rx, dz_index=0):
+    """Row m = (s, xo): output row y+s, x offset xo; column p: input x0-4+p;
+    input row j = y + a - ry.  Entry w[dz][j - (y+s)][p - 4 - xo]."""
+    A = np.zeros((16, 16), np.float64)
+    for m in range(16):
+        s, xo = divmod(m, 8)
+        dy = a - ry - s
+        for p in range(16):
+            dx = p - 4 - xo
+            if abs(dy) <= ry and abs(dx) <= rx:
+                A[m, p] = w[dz_index][dy + ry][dx + rx]
+    return A
+
+
+def tf32(x):
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32)
+
+
+@pytest.mark.parametrize("ndim,r", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2), (1, 3)])
+def test_tf32_operands_decode_to_banded_kernel_rows(ndim, r):
+    gen = np.random.default_rng(100 + r)
+    w = gen.standard_normal((2 * r + 1,) * ndim).astype(np.float32)
+    p = spider.Plan(w, (8,) * ndim, "box", "tf32")
+    words, meta = p.operands()
+    ry = r if ndim >= 2 else 0
+    rz = r if ndim == 3 else 0
+    w3 = w.reshape((2 * rz + 1, 2 * ry + 1, 2 * r + 1))
+    na = 2 * ry + 2
+    assert words.size == (2 * rz + 1) * na * 128 and meta.size == (2 * rz + 1) * na * 32
+    words = words.reshape(-1, 32, 4)
+    meta = meta.reshape(-1, 32)
+    for dzi in range(2 * rz + 1):
+        for a in range(na):
+            got = decode_tf32(words[dzi * na + a], meta[dzi * na + a])
+            want = tf32(expected_window(w3, a, ry, r, dzi))
+            assert np.array_equal(got, want), (dzi, a)
+    p.close()
+
+
+def test_window_matrices_are_the_papers_banded_K():
+    # The 8 x 16 half of a window matrix for one kernel row is the paper's
+    # banded K (Sec. 3.1.1) for L = 8 outputs shifted into the 16-wide window:
+    # K[m][n] = w[n - m] for 0 <= n - m <= 2r, placed at window column n + 4 - r.
+    from oracle import lowered
+    for r in (1, 2, 3):
+        w_row = np.arange(1, 2 * r + 2, dtype=np.float64)
+        K = lowered.kernel_matrix(w_row, L=8)              # 8 x (2r + 8)
+        win = expected_window(w_row.reshape(1, 1, -1), 0, 0, r)[:8]
+        assert np.array_equal(win[:, 4 - r:4 - r + K.shape[1]], K)
+        assert np.count_nonzero(win) == np.count_nonzero(K)
+
+
+def test_fragment_permutation_is_a_strided_swap_giving_1_2_and_2_4():
+    # the permutation places the members of every 1:2 pair 8 window positions
+    # apart; with a band of 2r+1 <= 7 positions the permuted K is 1:2 and 2:4
+    from oracle import lowered
+    perm = np.array([phi(k) for k in range(16)])
+    assert sorted(perm) == list(range(16))
+    for c in range(8):
+        assert abs(perm[2 * c] - perm[2 * c + 1]) == 8
+    for r in (1, 2, 3):
+        band = expected_window(np.ones((1, 1, 2 * r + 1)), 0, 0, r)[:8] != 0
+        permuted = band[:, perm]
+        assert lowered.is_1_2(permuted) and lowered.is_2_4(permuted)
+        assert not lowered.is_2_4(band)
+
+
+@pytest.mark.parametrize("prec", ["f16x2", "bf16x3"])
+def test_split_operands_have_expected_layout(prec):
+    w = np.random.default_rng(3).uniform(0, 1, (7, 7)).astype(np.float32)
+    w /= w.sum()
+    p = spider.Plan(w, (16, 16), "box", prec)
+    words, meta = p.operands()
+    combos = (3 + 1) + 8                    # (ry+1) hi*hi combos + (2ry+2) correction combos
+    assert words.size == combos * 128 and meta.size == combos * 32
+    # metadata nibbles: two increasing 2-bit indices per group, lanes q >= 2 unused
+    m = meta.reshape(combos, 32)
+    for c in range(combos):
+        for lane in range(32):
+            if lane % 4 >= 2:
+                assert m[c, lane] == 0
+                continue
+            for k in range(8):
+                nib = (int(m[c, lane]) >> (4 * k)) & 0xF
+                assert (nib & 3) < (nib >> 2)
+    p.close()

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 error after the full step count, and the largest
+point error relative to the largest |reference| value) follow the error
+model of the arithmetic: TF32 rounds grid values and weights to 11
+significant bits every step (unit roundoff 2^-11); the FP16 hi/lo split
+carries about 22 bits, the BF16 hi/lo split about 16 bits; the CUDA-core
+comparator is plain FP32.  Integer inputs whose every intermediate is exactly
+representable must match bit for bit in every engine and precision.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+spider = pytest.importorskip("paper_2506_22035_gb300")
+
+# (relative L2, max point error / max |ref|)
+TOL = {
+    ("sparse_tc", "tf32"): (3e-3, 1e-2),
+    ("sparse_tc", "f16x2"): (2e-5, 1e-4),
+    ("sparse_tc", "bf16x3"): (2e-4, 1e-3),
+    ("dense_tc", "tf32"): (3e-3, 1e-2),
+    ("cuda_core", "tf32"): (2e-6, 2e-5),
+}
+ALL = list(TOL)
+
+
+def gpu_run(u0, w, steps, shape="box", prec="tf32", engine="sparse_tc"):
+    plan = spider.Plan(w, u0.shape, shape, prec, engine)
+    a = torch.from_numpy(np.ascontiguousarray(u0, np.float32)).cuda()
+    b = torch.full_like(a, float("nan"))
+    plan.run(a, b, steps)
+    plan.sync()
+    torch.cuda.synchronize()
+    out = b.cpu().numpy()
+    assert np.array_equal(a.cpu().numpy(), u0)          # input preserved
+    plan.close()
+    return out
+
+
+def check_close(got, ref, key):
+    rel_tol, max_tol = TOL[key]
+    assert np.all(np.isfinite(got))
+    ref_norm = np.linalg.norm(ref)
+    rel = np.linalg.norm(got - ref) / ref_norm if ref_norm > 0 else np.linalg.norm(got)
+    mx = np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)
+    assert rel <= rel_tol, (key, rel)
+    assert mx <= max_tol, (key, mx)
+    return rel
+
+
+def int_case(shape, r, seed):
+    g = np.random.default_rng(seed)
+    u = g.integers(-1, 2, size=shape).astype(np.float32)
+    w = g.integers(-1, 2, size=(2 * r + 1,) * len(shape)).astype(np.float32)
+    return u, w
+
+
+@pytest.mark.parametrize("key", ALL)
+@pytest.mark.parametrize("shape,r,steps", [((37, 75), 1, 3), ((70, 131), 2, 2), ((33, 200), 3, 1),
+                                           ((6, 9, 70), 1, 2), ((300,), 2, 3)])
+def test_integer_inputs_bit_exact(key, shape, r, steps):
+    # every intermediate is an integer below 2^11 in magnitude, exact in TF32,
+    # FP16 and BF16 hi/lo splits: the lowered sparse product must equal the
+    # direct sweep exactly (the swap is a pure permutation)
+    engine, prec = key
+    u, w = int_case(shape, r, seed=r * 10 + len(shape))
+    ref = oracle.stencil(u, w, steps)
+    assert np.max(np.abs(ref)) < 2048
+    got = gpu_run(u, w, steps, "box", prec, engine)
+    assert np.array_equal(got.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("key", ALL)
+def test_heat2d_512_full_workload(key):
+    wl = si.HEAT2D_512
+    u0, w = si.workload_inputs(wl)
+    ref = oracle.stencil(u0, w, wl.steps)
+    got = gpu_run(u0, w, wl.steps, "star", key[1], key[0])
+    check_close(got, ref, key)
+
+
+@pytest.mark.parametrize("key", ALL)
+@pytest.mark.parametrize("shape", [(200, 333), (129, 64), (64, 260)])
+def test_box2d_r3_ragged(key, shape):
+    u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=shape)
+    ref = oracle.stencil(u0, w, 12)
+    got = gpu_run(u0, w, 12, "box", key[1], key[0])
+    check_close(got, ref, key)
+
+
+@pytest.mark.parametrize("key", ALL)
+@pytest.mark.parametrize("wl,shape", [(si.HEAT3D_512, (20, 33, 70)), (si.BOX3D_512, (17, 40, 64)),
+                                      (si.BOX3D_512, (9, 9, 200))])
+def test_3d_small(key, wl, shape):
+    u0, w = si.workload_inputs(wl, extents=shape)
+    ref = oracle.stencil(u0, w, 6)
+    got = gpu_run(u0, w, 6, wl.shape, key[1], key[0])
+    check_close(got, ref, key)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("shape_kind", ["star", "box"])
+def test_all_radii_tf32(r, ndim, shape_kind):
+    g = si.rng(9, r + 3 * ndim)
+    ext = (45, 70) if ndim == 2 else (10, 21, 37)
+    u0 = si.grid(ext, -1, 1, g)
+    w = si.normalised_coeffs(ndim, r, shape_kind, g)
+    ref = oracle.stencil(u0, w, 4)
+    got = gpu_run(u0, w, 4, shape_kind, "tf32")
+    check_close(got, ref, ("sparse_tc", "tf32"))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 50), (50, 1), (3, 5), (65, 129), (31, 67), (7,), (2, 3, 1)])
+@pytest.mark.parametrize("steps", [0, 1, 2])
+def test_edge_shapes_and_step_counts(shape, steps):
+    u, w = int_case(shape, 1, seed=sum(shape) + steps)
+    ref = oracle.stencil(u, w, steps)
+    for key in (("sparse_tc", "tf32"), ("sparse_tc", "f16x2"), ("cuda_core", "tf32")):
+        got = gpu_run(u, w, steps, "box", key[1], key[0])
+        assert np.array_equal(got.astype(np.float64), ref), (key, shape, steps)
+
+
+def test_run_host_matches_device_run():
+    u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(130, 260))
+    plan = spider.Plan(w, u0.shape, "box", "tf32")
+    host = plan.run_host(u0, 7)
+    dev = gpu_run(u0, w, 7)
+    assert np.array_equal(host, dev)
+    plan.close()
+
+
+def test_repeat_runs_are_bitwise_identical():
+    u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(512, 1024))
+    a = gpu_run(u0, w, 5)
+    b = gpu_run(u0, w, 5)
+    assert np.array_equal(a, b)
+
+
+def test_fp64_norms_match_numpy():
+    g = np.random.default_rng(1)
+    a = g.standard_normal(1_000_003).astype(np.float32)
+    ref = a.astype(np.float64) + g.standard_normal(a.size) * 1e-3
+    ta, tr = torch.from_numpy(a).cuda(), torch.from_numpy(ref).cuda()
+    saa, srr, sdd, md = spider.norms_fp64(ta, tr)
+    a64 = a.astype(np.float64)
+    np.testing.assert_allclose(saa, np.sum(a64 * a64), rtol=1e-12)
+    np.testing.assert_allclose(srr, np.sum(ref * ref), rtol=1e-12)
+    np.testing.assert_allclose(sdd, np.sum((a64 - ref) ** 2), rtol=1e-12)
+    assert md == np.max(np.abs(a64 - ref))
+
+
+@pytest.mark.parametrize("prec", ["tf32", "f16x2", "bf16x3"])
+def test_constant_field_invariant_on_gpu(prec):
+    # dyadic weights summing to 1 and a dyadic constant are exact in every
+    # precision: interior points farther than steps*r from the boundary keep
+    # the constant exactly; the check runs in FP64 on the GPU.
+    w = np.zeros((3, 3), np.float32)
+    w[1, 1] = 0.5
+    w[0, 1] = w[2, 1] = w[1, 0] = w[1, 2] = 0.125
+    u0 = np.full((200, 300), 0.75, np.float32)
+    plan = spider.Plan(w, u0.shape, "star", prec)
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    plan.run(a, b, 9)
+    assert spider.constant_check_fp64(b, u0.shape, 10, 0.75) == 0.0
+    assert spider.constant_check_fp64(b, u0.shape, 0, 0.75) > 0.0       # the zero halo leaks in
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "f16x2", "bf16x3"])
+def test_box2d_r3_8192_full_size_sampled(prec):
+    # the benchmark workload at full size and full step count; the oracle
+    # evaluates sampled points exactly through their dependency cones
+    wl = si.BOX2D_R3_8192
+    u0, w = si.workload_inputs(wl)
+    plan = spider.Plan(w, u0.shape, "box", prec)
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    plan.run(a, b, wl.steps)
+    plan.sync()
+    n = u0.shape[0]
+    pts = [(0, 0), (n - 1, n - 1), (0, n // 2), (n // 2, n - 1), (4097, 1234), (777, 8000)]
+    ref = oracle.stencil_points(u0, w, wl.steps, pts)
+    got = b[tuple(np.array(pts).T)].cpu().numpy().astype(np.float64)
+    rms = np.sqrt(spider.norms_fp64(b)[0] / b.numel())
+    tol = {"tf32": 2e-2, "f16x2": 1e-4, "bf16x3": 1e-3}[prec]
+    assert np.all(np.abs(got - ref) <= tol * rms), (got, ref, rms)
+    plan.close()
