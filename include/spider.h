@@ -134,6 +134,30 @@ spider_status spider_run(spider_plan plan, const float* grid_in, float* grid_out
 spider_status spider_run_host(spider_plan plan, const float* host_in, float* host_out, int64_t steps,
                               cudaStream_t stream);
 
+/* spider_run_static -- spider_run that allocates no device memory.
+ * The paper has no counterpart: this is an addition of the library.
+ *
+ * For callers that cannot call cudaMalloc: an application whose own memory
+ * pool has already reserved the GPU's memory (a further cudaMalloc would
+ * fail), or a latency-critical loop that cannot accept the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree.  Instead of the
+ * plan-owned device buffers spider_run allocates on first use, it works in
+ * fixed-size __device__ arrays of the library: a scratch grid of at most
+ * 4,194,304 points (16 MiB) plus 84 KiB for packed operands, metadata and
+ * coefficients.  Every GPU that loads the library holds these arrays until
+ * the process exits.
+ *  grid_in, grid_out, steps, stream: as for spider_run.
+ * Grids with more than 4,194,304 points return SPIDER_ERR_INVALID and nothing
+ * is done.  The first call on each device looks up the arrays' device
+ * addresses (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Each call loads its plan's operands into
+ * the shared arrays and clears the shared status word, and all calls share
+ * one scratch grid, so calls that overlap on the GPU (other streams or
+ * threads) race and corrupt each other's results.  A device-side wait that
+ * runs out is not reported by this entry point. */
+spider_status spider_run_static(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
+                                cudaStream_t stream);
+
 /* Blocks until the plan's work on `stream` is done and reports any
  * device-side error (SPIDER_ERR_TIMEOUT for an expired wait). */
 spider_status spider_plan_sync(spider_plan plan, cudaStream_t stream);

@@ -37,6 +37,7 @@ SIGNATURES = {
                                      ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t)]),
     "spider_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "spider_run_static": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_plan_sync": (c_int, [c_void_p, c_void_p]),
     "spider_plan_destroy": (None, [c_void_p]),
     "spider_batch": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),

@@ -1,0 +1,66 @@
+"""spider_run_static, the entry point that allocates no device memory.
+
+It exists for callers that cannot call cudaMalloc -- an application whose
+own memory pool already holds the GPU's memory, or a latency-critical loop
+that cannot accept cudaMalloc's implicit synchronisation -- and works in the
+library's fixed-size __device__ arrays instead of plan-owned buffers.  This
+file is collected last so that a run stopping at its first failure has
+already run every other test; it also passes when run alone.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import stencil_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _lib():
+    from paper_2506_22035_gb300 import _native, build
+    build.build()
+    return _native
+
+
+def _run(native, fn, plan, a, b, steps):
+    st = getattr(native.load(), fn)(plan.handle, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                    steps, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    native.check(st, fn)
+
+
+def _rel(x, y):
+    return float(torch.linalg.vector_norm((x - y).double()) / torch.linalg.vector_norm(y.double()))
+
+
+def test_static_entry_point_matches_spider_run_on_two_calls_in_a_row():
+    native = _lib()
+    import paper_2506_22035_gb300 as spider
+
+    # grids above the static limit are refused before any device work
+    big = spider.Plan(np.ones((3, 3), np.float32), (2049, 2049), "box", "tf32")
+    # far-apart addresses that the size check rejects before they could be used
+    st = native.load().spider_run_static(big.handle, ctypes.c_void_p(1 << 40), ctypes.c_void_p(1 << 41), 1, None)
+    assert st == native.SPIDER_ERR_INVALID
+    assert b"4194304" in native.load().spider_last_error()
+    big.close()
+
+    cases = [
+        (si.BOX2D_R3_8192, (300, 520), 7, "tf32"),      # odd step count
+        (si.HEAT3D_512, (20, 33, 72), 6, "f16x2"),      # even step count, another plan's operands
+    ]
+    for wl, ext, steps, prec in cases:
+        u0, w = si.workload_inputs(wl, extents=ext)
+        plan = spider.Plan(w, ext, wl.shape, prec)
+        a = torch.from_numpy(u0).cuda()
+        ref = torch.empty_like(a)
+        got = torch.full_like(a, float("nan"))
+        _run(native, "spider_run", plan, a, ref, steps)
+        _run(native, "spider_run_static", plan, a, got, steps)
+        torch.cuda.synchronize()
+        tol = 3e-3 if prec == "tf32" else 2e-5              # the parity tests' tolerances
+        assert torch.isfinite(got).all()
+        assert _rel(got, ref) <= tol
+        plan.close()
