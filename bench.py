@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
     ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
+    ap.add_argument("--steps-per-pass", type=int, default=None,
+                    help="time steps fused per HBM pass (default: chosen by spider_plan_autotune)")
+    ap.add_argument("--tile-variant", type=int, default=None)
     ap.add_argument("--extents", type=int, nargs="+", default=None,
                     help="override the grid size (same distributions; for profiling runs)")
     ap.add_argument("--no-comparators", action="store_true")
@@ -64,6 +67,7 @@ def parse_args():
     a = ap.parse_args()
     if a.steps is None:
         a.steps = DEFAULT_STEPS[a.workload]
+
     a.warmup = max(3, a.warmup)
     return a
 
@@ -228,7 +232,7 @@ def run_reference(a):
 def workload_config(wl, a, extra=None):
     cfg = {"workload": f"{wl.name}, {wl.steps} time steps", "stencil": f"{wl.shape} r={wl.r} {wl.ndim}-D",
            "extents": list(wl.extents), "time_steps": wl.steps, "precision": a.precision, "engine": a.engine,
-           "steps_per_pass": 1, "global_batch": 1,
+           "steps_per_pass": a.steps_per_pass, "tile_variant": a.tile_variant, "global_batch": 1,
            "l2": "inputs larger than L2" if 4 * int(np.prod(wl.extents)) > L2_BYTES else "L2 flushed between timed runs",
            "parallelism": f"replicas{a.gpus}"}
     if extra:
@@ -284,6 +288,21 @@ def run_spider(a):
     plan = spider.Plan(w, wl.extents, wl.shape, a.precision, a.engine)
     a_in = torch.from_numpy(u0).to(dev)
     b_out = torch.empty_like(a_in)
+
+    def configure(p):
+        """Steps per pass and tile variant: given on the command line, else
+        picked by the library's autotuner (outside the timed region)."""
+        if a.steps_per_pass is None and a.tile_variant is None:
+            return p.autotune(a_in, b_out, wl.steps, stream)
+        t = a.steps_per_pass or 1
+        v = a.tile_variant or 0
+        if t > 1:
+            p.set_steps_per_pass(t)
+        p.set_tile_variant(v)
+        return t, v
+
+    chosen_T, chosen_v = configure(plan)
+    a.steps_per_pass, a.tile_variant = chosen_T, chosen_v
     flush = None if grid_bytes > L2_BYTES else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(a.warmup):
@@ -306,7 +325,8 @@ def run_spider(a):
         t = torch.tensor([dt], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t.item())
-    launches_per_run = wl.steps  # one launch per time step (steps_per_pass = 1)
+    T = a.steps_per_pass
+    launches_per_run = wl.steps // T + (1 if wl.steps % T else 0)  # one launch per pass
     total_launches = a.steps * launches_per_run
     value = world * pts * wl.steps * a.steps / dt / 1e9
     per_launch_s = dt / total_launches
@@ -314,7 +334,7 @@ def run_spider(a):
     result = None
     if rank == 0:
         peaks, peak_kind = measured_peaks()
-        alg_bytes = 8.0 * pts  # read every point once and write it once per step
+        alg_bytes = 8.0 * pts  # read every point once and write it once per pass
         achieved = alg_bytes / per_launch_s / 1e9
         kernel_key = f"stencil_step_kernel {wl.name} {a.engine} {a.precision}"
         traffic = traffic_from_profiles(kernel_key)
@@ -359,13 +379,15 @@ def run_spider(a):
             if (eng, prec) == (a.engine, a.precision):
                 continue
             p2 = spider.Plan(w, wl.extents, wl.shape, prec, eng)
+            t2, v2 = p2.autotune(a_in, b_out, wl.steps, stream)   # each comparator at its own best setting
             iters = max(3, a.steps // 10)
             for _ in range(2):
                 p2.run(a_in, b_out, wl.steps, stream)
             torch.cuda.synchronize(dev)
             d2 = time_runs(p2, a_in, b_out, wl.steps, iters, flush, stream)
             p2.sync(stream)
-            comps[f"{eng}/{prec}"] = pts * wl.steps * iters / d2 / 1e9
+            comps[f"{eng}/{prec}"] = {"value": pts * wl.steps * iters / d2 / 1e9, "steps_per_pass": t2,
+                                      "tile_variant": v2}
             p2.close()
         result["comparators"] = comps
 

@@ -104,6 +104,23 @@ spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
  * build does not support for the plan's stencil return SPIDER_ERR_UNSUPPORTED. */
 spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);
 
+/* Tile shape of the fused kernels: 0 = warp units of 8 output rows,
+ * 1 = 16 rows (more independent MMAs per warp, more registers), 2 = 8 rows
+ * with registers capped so three CTAs share an SM.  Any other value returns
+ * SPIDER_ERR_INVALID.  spider_plan_autotune sets it. */
+spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
+
+/* spider_plan_autotune -- measures the plan's configurations on the caller's
+ * grids and keeps the fastest: time steps per pass 1..4 (2-D stencils) and
+ * the tile variant.  Each candidate runs `steps` steps from grid_in into
+ * grid_out (device grids as for spider_run; grid_out is overwritten) once to
+ * warm up and twice timed with CUDA events on `stream`; the call is
+ * synchronous.  Results are cached per (ndim, radius, shape, precision,
+ * engine, grid-size bucket), so later plans of the same kind reuse them
+ * without timing.  *steps_per_pass / *variant (nullable) receive the choice. */
+spider_status spider_plan_autotune(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
+                                   cudaStream_t stream, int* steps_per_pass, int* variant);
+
 /* Reads back the plan's packed operands (host copies) for inspection and
  * testing.  Any pointer may be NULL; sizes are in 32-bit words.
  *   n_operand_words / operand_words : tensor-core A fragments, per

@@ -65,6 +65,18 @@ class Plan:
     def set_steps_per_pass(self, t: int) -> None:
         check(_native.load().spider_plan_set_steps_per_pass(self._h, int(t)), "spider_plan_set_steps_per_pass")
 
+    def set_tile_variant(self, v: int) -> None:
+        check(_native.load().spider_plan_set_tile_variant(self._h, int(v)), "spider_plan_set_tile_variant")
+
+    def autotune(self, grid_in, grid_out, steps: int, stream=None):
+        """Times the candidate configurations on these grids and keeps the
+        fastest; returns (steps_per_pass, tile_variant)."""
+        t, v = ctypes.c_int(), ctypes.c_int()
+        check(_native.load().spider_plan_autotune(self._h, _ptr(grid_in), _ptr(grid_out), int(steps),
+                                                  _stream_handle(stream), ctypes.byref(t), ctypes.byref(v)),
+              "spider_plan_autotune")
+        return t.value, v.value
+
     def operands(self):
         lib = _native.load()
         na, nm = ctypes.c_size_t(), ctypes.c_size_t()

@@ -33,6 +33,9 @@ SIGNATURES = {
                                    c_int, ctypes.POINTER(c_void_p)]),
     "spider_plan_set_engine": (c_int, [c_void_p, c_int]),
     "spider_plan_set_steps_per_pass": (c_int, [c_void_p, c_int]),
+    "spider_plan_set_tile_variant": (c_int, [c_void_p, c_int]),
+    "spider_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int),
+                                     ctypes.POINTER(c_int)]),
     "spider_plan_operands": (c_int, [c_void_p, ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t),
                                      ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t)]),
     "spider_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),

@@ -1,5 +1,6 @@
 // The C ABI (include/spider.h): plan lifecycle, spider_run, spider_run_host.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -112,16 +113,24 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   ctx.plan = p;
   ctx.stream = stream;
   ctx.sms = device_sm_count();
+  // Passes of T fused time steps (2-D grids whose rows and buffers are
+  // 16-byte aligned, as TMA requires), then one pass with the remainder.
+  int T = p->steps_per_pass;
+  auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  if (T > 1 && !(p->ndim == 2 && p->nx % 4 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch))) T = 1;
+  const int64_t full = steps / T;
+  const int rem = (int)(steps % T);
+  const int64_t npasses = full + (rem ? 1 : 0);
   // Ping-pong between out and the scratch grid; the parity of the first
-  // destination makes the last step land in out.
+  // destination makes the last pass land in out.
   float* bufs[2] = {out, p->dev.scratch};
-  const int first = (steps % 2 == 1) ? 0 : 1;
-  for (int64_t t = 0; t < steps; ++t) {
-    ctx.dst = bufs[(first + t) % 2];
-    ctx.src = (t == 0) ? in : bufs[(first + t - 1) % 2];
-    cudaError_t e = launch_step(ctx);
+  const int first = (npasses % 2 == 1) ? 0 : 1;
+  for (int64_t k = 0; k < npasses; ++k) {
+    ctx.dst = bufs[(first + k) % 2];
+    ctx.src = (k == 0) ? in : bufs[(first + k - 1) % 2];
+    cudaError_t e = launch_pass(ctx, k < full ? T : rem);
     if (e == cudaErrorNotSupported) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil/engine");
-    if (e != cudaSuccess) return cuda_fail(e, "stencil step launch");
+    if (e != cudaSuccess) return cuda_fail(e, "stencil pass launch");
   }
   return SPIDER_OK;
 }
@@ -213,7 +222,8 @@ spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
 spider_status spider_plan_set_steps_per_pass(spider_plan p, int steps_per_pass) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
   if (steps_per_pass < 1) return fail(SPIDER_ERR_INVALID, "steps_per_pass must be >= 1");
-  if (steps_per_pass != 1) return fail(SPIDER_ERR_UNSUPPORTED, "temporal fusion is not built for this stencil");
+  if (steps_per_pass > 1 && (p->ndim != 2 || steps_per_pass > 4))
+    return fail(SPIDER_ERR_UNSUPPORTED, "temporal fusion is built for 2-D stencils, 2..4 steps per pass");
   p->steps_per_pass = steps_per_pass;
   return SPIDER_OK;
 }

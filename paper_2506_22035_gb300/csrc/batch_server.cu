@@ -2,7 +2,7 @@
 #include "spider_internal.h"
 
 namespace spider {
-spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
+
 }
 using namespace spider;
 

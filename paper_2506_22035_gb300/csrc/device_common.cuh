@@ -79,7 +79,22 @@ __device__ __forceinline__ float4 lds128(const float* p) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(smem_u32(p)));
+               : "r"(smem_u32(p))
+               : "memory");
+  return v;
+}
+
+// 16-byte shared-memory load at shared-window address `addr` + OFF bytes;
+// the constant offset folds into the instruction.  Not volatile: the
+// compiler may schedule it early (the memory clobber keeps it on the right
+// side of barriers and stores).
+template <int OFF>
+__device__ __forceinline__ float4 lds128_at(uint32_t addr) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr), "n"(OFF)
+               : "memory");
   return v;
 }
 
@@ -106,9 +121,12 @@ __device__ __forceinline__ float2 unpack_bf162(uint32_t v) {
   return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xFFFF0000u));
 }
 
+// The MMA wrappers are not volatile: each is a pure function of its operands,
+// so the compiler is free to interleave them with the loads of later rows.
+
 // D += A(sparse 1:2, TF32) * B, m16n8k16.
 __device__ __forceinline__ void mma_sp_tf32(float (&d)[4], const uint4& a, uint32_t e, const uint32_t (&b)[4]) {
-  asm volatile(
+  asm(
       "mma.sp::ordered_metadata.sync.aligned.m16n8k16.row.col.f32.tf32.tf32.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9,%10,%11}, {%0,%1,%2,%3}, %12, 0x0;"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -117,7 +135,7 @@ __device__ __forceinline__ void mma_sp_tf32(float (&d)[4], const uint4& a, uint3
 
 // D += A(dense TF32) * B, m16n8k8.
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -127,7 +145,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint4& a, uint32_t
 // D += A(sparse 2:4, FP16) * B, m16n8k32.
 __device__ __forceinline__ void mma_sp_f16_k32(float (&d)[4], const uint4& a, uint32_t e, uint32_t b0, uint32_t b1,
                                                uint32_t b2, uint32_t b3) {
-  asm volatile(
+  asm(
       "mma.sp::ordered_metadata.sync.aligned.m16n8k32.row.col.f32.f16.f16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9,%10,%11}, {%0,%1,%2,%3}, %12, 0x0;"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -137,7 +155,7 @@ __device__ __forceinline__ void mma_sp_f16_k32(float (&d)[4], const uint4& a, ui
 // D += A(sparse 2:4, BF16) * B, m16n8k32.
 __device__ __forceinline__ void mma_sp_bf16_k32(float (&d)[4], const uint4& a, uint32_t e, uint32_t b0, uint32_t b1,
                                                 uint32_t b2, uint32_t b3) {
-  asm volatile(
+  asm(
       "mma.sp::ordered_metadata.sync.aligned.m16n8k32.row.col.f32.bf16.bf16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9,%10,%11}, {%0,%1,%2,%3}, %12, 0x0;"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])

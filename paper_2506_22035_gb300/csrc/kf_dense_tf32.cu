@@ -1,0 +1,6 @@
+// Instantiates the fused (T = 2..4 steps per pass) DenseTF32 kernels.
+#include "launch_impl.cuh"
+
+namespace spider {
+cudaError_t launch_fused_dense_tf32(int r, int T, const LaunchCtx& ctx) { return launch_fused_mode<Mode::DenseTF32>(r, T, ctx); }
+}  // namespace spider

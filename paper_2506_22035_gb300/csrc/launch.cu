@@ -69,3 +69,22 @@ cudaError_t launch_step(const LaunchCtx& ctx) {
 }
 
 }  // namespace spider
+
+namespace spider {
+
+cudaError_t launch_pass(const LaunchCtx& ctx, int T) {
+  if (T <= 1) return launch_step(ctx);
+  const spider_plan_t* p = ctx.plan;
+  switch (p->engine) {
+    case SPIDER_ENGINE_CUDA_CORE: return launch_fused_cuda_core(p->r, T, ctx);
+    case SPIDER_ENGINE_DENSE_TC: return launch_fused_dense_tf32(p->r, T, ctx);
+    default: break;
+  }
+  switch (p->prec) {
+    case SPIDER_F16X2: return launch_fused_sp_f16x2(p->r, T, ctx);
+    case SPIDER_BF16X3: return launch_fused_sp_bf16x3(p->r, T, ctx);
+    default: return launch_fused_sp_tf32(p->r, T, ctx);
+  }
+}
+
+}  // namespace spider

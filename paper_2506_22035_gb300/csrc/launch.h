@@ -29,6 +29,16 @@ cudaError_t launch_sp_bf16x3(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_dense_tf32(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_cuda_core(int cls, int r, const LaunchCtx& ctx);
 
+// Fused passes of T = 2..4 time steps (2-D stencils, TMA-aligned grids).
+// cudaErrorNotSupported when no fused kernel applies; the caller then runs
+// single steps.
+cudaError_t launch_pass(const LaunchCtx& ctx, int T);
+cudaError_t launch_fused_sp_tf32(int r, int T, const LaunchCtx& ctx);
+cudaError_t launch_fused_sp_f16x2(int r, int T, const LaunchCtx& ctx);
+cudaError_t launch_fused_sp_bf16x3(int r, int T, const LaunchCtx& ctx);
+cudaError_t launch_fused_dense_tf32(int r, int T, const LaunchCtx& ctx);
+cudaError_t launch_fused_cuda_core(int r, int T, const LaunchCtx& ctx);
+
 // Builds a 3-D tiled tensor map over a float32 grid (nz, ny, nx) with the
 // given box; out-of-range box elements read as zero.  Returns false if the
 // grid cannot be described (row pitch or base not 16-byte aligned).

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "launch.h"
+#include "fused_kernels.cuh"
 #include "stencil_kernels.cuh"
 
 namespace spider {
@@ -74,6 +75,91 @@ cudaError_t launch_mode(int cls, int r, const LaunchCtx& ctx) {
     case 1: return launch_class<1, MODE>(cls, ctx);
     case 2: return launch_class<2, MODE>(cls, ctx);
     case 3: return launch_class<3, MODE>(cls, ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// ---- temporal fusion (2-D) ----------------------------------------------
+template <class F, Mode MODE>
+cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  if (p->ndim != 2) return cudaErrorNotSupported;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, 1, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
+  auto kern = fused_step_kernel<F, MODE>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, F::kThreads, F::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = 1;
+  a.tiles_x = (int)((p->nx + F::BX - 1) / F::BX);
+  a.tiles_y = (int)((p->ny + F::BY - 1) / F::BY);
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.use_tma = 1;
+  const long long ntiles = (long long)a.tiles_x * a.tiles_y;
+  if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
+  kern<<<grid, F::kThreads, F::kSmemBytes, ctx.stream>>>(map, a);
+  return cudaGetLastError();
+}
+
+// Fused tile shapes: level 1 is 64 rows x 16 segments (two N-tiles), so the
+// output tile is BY = 64 - 2r(T-1) rows x BX = 8 (17 - T) columns; 8 warps;
+// warp units of H rows x 8 segments.  Variants: 0 -> H = 8; 1 -> H = 16;
+// 2 -> H = 8 with registers capped for 3 CTAs per SM.
+template <int R, int T, int H, int MINB>
+using FusedTile = FuseCfg<R, T, 64 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB>;
+
+template <Mode MODE, int R, int H, int MINB>
+cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
+  switch (T) {
+    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB>, MODE>(ctx);
+    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB>, MODE>(ctx);
+    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB>, MODE>(ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <Mode MODE, int R>
+cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
+  switch (ctx.plan->tile_variant) {
+    case 1: return launch_fused_rh<MODE, R, 16, 1>(T, ctx);
+    case 2: return launch_fused_rh<MODE, R, 8, 3>(T, ctx);
+    default: return launch_fused_rh<MODE, R, 8, 1>(T, ctx);
+  }
+}
+
+template <Mode MODE>
+cudaError_t launch_fused_mode(int r, int T, const LaunchCtx& ctx) {
+  switch (r) {
+    case 1: return launch_fused_r<MODE, 1>(T, ctx);
+    case 2: return launch_fused_r<MODE, 2>(T, ctx);
+    case 3: return launch_fused_r<MODE, 3>(T, ctx);
     default: return cudaErrorNotSupported;
   }
 }

@@ -46,8 +46,6 @@ inline int phi_16bit(int kk) {  // kk in [0, 16) within one K half
 }
 
 // -------------------------------------------------------------- the plan
-enum class Term : int { Single = 0 };
-
 struct DeviceState {
   int device = -1;
   uint32_t* a_words = nullptr;     // packed A fragments
@@ -71,8 +69,9 @@ struct spider_plan_t {
   spider_precision prec = SPIDER_TF32;
   spider_engine engine = SPIDER_ENGINE_SPARSE_TC;
   int steps_per_pass = 1;
+  int tile_variant = 0;                  // fused warp-unit height: 0 -> 8 rows, 1 -> 16 rows
   std::vector<float> w;                  // (2rz+1)(2ry+1)(2rx+1), [dz][dy][dx]
-  // Packed operands, see plan.cpp for the layouts.
+  // Packed operands, see plan.cu for the layouts.
   int n_arows = 0;                       // A matrices per split term = (2rz+1)(2ry+2)
   int n_combos = 0;                      // A operands actually issued per dz-plane set
   std::vector<uint32_t> a_words;         // [combo][lane][4]  (dense TF32: [arow][lane][8])
@@ -96,5 +95,8 @@ float tf32_value(float x);
 
 // Number of A "combos" (register operands) for a precision, per dz plane.
 int combos_per_plane(spider_precision prec, int ry);
+
+// api.cu: enqueue `steps` steps in -> out on `stream` (plan lock held by the caller).
+spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
 
 }  // namespace spider

@@ -67,37 +67,48 @@ struct TileCfg {
 // input value (plane, first input row of the warp tile); rows are SX floats
 // apart.  acc[pp] accumulates output rows (2pp, 2pp+1) of the warp tile.
 
-template <class C>
-__device__ __forceinline__ void plane_sp_tf32(const float* row0, const uint4 (&A)[C::NA],
-                                              const uint32_t (&E)[C::NA], float (&acc)[C::H / 2][4]) {
+// ROUND = false when the source already holds TF32 values (fused
+// intermediate levels), so the 13 low mantissa bits are already zero.
+template <class C, int SP, bool ROUND, int JJ>
+__device__ __forceinline__ void sp_tf32_row(uint32_t addr, const uint4 (&A)[C::NA], const uint32_t (&E)[C::NA],
+                                            float (&acc)[C::H / 2][4]) {
+  const float4 v = lds128_at<JJ * SP * 4>(addr);
+  const uint32_t b[4] = {ROUND ? cvt_tf32(v.x) : __float_as_uint(v.x), ROUND ? cvt_tf32(v.y) : __float_as_uint(v.y),
+                         ROUND ? cvt_tf32(v.z) : __float_as_uint(v.z), ROUND ? cvt_tf32(v.w) : __float_as_uint(v.w)};
 #pragma unroll
-  for (int jj = 0; jj < C::H + 2 * C::RY; ++jj) {
-    const float4 v = lds128(row0 + jj * C::SX);
-    const uint32_t b[4] = {cvt_tf32(v.x), cvt_tf32(v.y), cvt_tf32(v.z), cvt_tf32(v.w)};
-#pragma unroll
-    for (int pp = 0; pp < C::H / 2; ++pp) {
-      const int a = jj - 2 * pp;
-      if (a >= 0 && a < C::NA) mma_sp_tf32(acc[pp], A[a], E[a], b);
-    }
+  for (int pp = 0; pp < C::H / 2; ++pp) {
+    const int a = JJ - 2 * pp;
+    if (a >= 0 && a < C::NA) mma_sp_tf32(acc[pp], A[a], E[a], b);
   }
+  if constexpr (JJ + 1 < C::H + 2 * C::RY) sp_tf32_row<C, SP, ROUND, JJ + 1>(addr, A, E, acc);
 }
 
-template <class C>
-__device__ __forceinline__ void plane_dense_tf32(const float* row0, const uint4 (&A)[C::NA][2],
-                                                 float (&acc)[C::H / 2][4]) {
+template <class C, int SP = C::SX, bool ROUND = true>
+__device__ __forceinline__ void plane_sp_tf32(const float* row0, const uint4 (&A)[C::NA],
+                                              const uint32_t (&E)[C::NA], float (&acc)[C::H / 2][4]) {
+  sp_tf32_row<C, SP, ROUND, 0>(smem_u32(row0), A, E, acc);
+}
+
+template <class C, int SP, bool ROUND, int JJ>
+__device__ __forceinline__ void dense_tf32_row(uint32_t addr, const uint4 (&A)[C::NA][2], float (&acc)[C::H / 2][4]) {
+  const float4 v = lds128_at<JJ * SP * 4>(addr);
+  const uint32_t b[4] = {ROUND ? cvt_tf32(v.x) : __float_as_uint(v.x), ROUND ? cvt_tf32(v.y) : __float_as_uint(v.y),
+                         ROUND ? cvt_tf32(v.z) : __float_as_uint(v.z), ROUND ? cvt_tf32(v.w) : __float_as_uint(v.w)};
 #pragma unroll
-  for (int jj = 0; jj < C::H + 2 * C::RY; ++jj) {
-    const float4 v = lds128(row0 + jj * C::SX);
-    const uint32_t b[4] = {cvt_tf32(v.x), cvt_tf32(v.y), cvt_tf32(v.z), cvt_tf32(v.w)};
-#pragma unroll
-    for (int pp = 0; pp < C::H / 2; ++pp) {
-      const int a = jj - 2 * pp;
-      if (a >= 0 && a < C::NA) {
-        mma_tf32(acc[pp], A[a][0], b[0], b[1]);
-        mma_tf32(acc[pp], A[a][1], b[2], b[3]);
-      }
+  for (int pp = 0; pp < C::H / 2; ++pp) {
+    const int a = JJ - 2 * pp;
+    if (a >= 0 && a < C::NA) {
+      mma_tf32(acc[pp], A[a][0], b[0], b[1]);
+      mma_tf32(acc[pp], A[a][1], b[2], b[3]);
     }
   }
+  if constexpr (JJ + 1 < C::H + 2 * C::RY) dense_tf32_row<C, SP, ROUND, JJ + 1>(addr, A, acc);
+}
+
+template <class C, int SP = C::SX, bool ROUND = true>
+__device__ __forceinline__ void plane_dense_tf32(const float* row0, const uint4 (&A)[C::NA][2],
+                                                 float (&acc)[C::H / 2][4]) {
+  dense_tf32_row<C, SP, ROUND, 0>(smem_u32(row0), A, acc);
 }
 
 // Split precisions (FP16 hi/lo with the lo parts scaled by 2^11, or BF16
@@ -128,26 +139,32 @@ __device__ __forceinline__ void mma_k32(float (&d)[4], const uint4& a, uint32_t 
   else mma_sp_f16_k32(d, a, e, b0, b1, b2, b3);
 }
 
-template <class C, bool BF16>
+template <class C, bool BF16, int SP, int JJ>
+__device__ __forceinline__ void sp_split_rows(uint32_t addr, const uint4 (&Am)[C::RY + 1],
+                                              const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
+                                              const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
+                                              float (&accC)[C::H / 2][4]) {
+  uint32_t hi0[2], lo0[2], hi1[2], lo1[2];
+  split4<C, BF16>(lds128_at<JJ * SP * 4>(addr), hi0, lo0);
+  split4<C, BF16>(lds128_at<(JJ + 1) * SP * 4>(addr), hi1, lo1);
+#pragma unroll
+  for (int pp = 0; pp < C::H / 2; ++pp) {
+    const int a0 = JJ - 2 * pp;  // even; rows JJ, JJ+1 use A indices a0, a0+1
+    if (a0 >= 0 && a0 + 1 < C::NA) {
+      mma_k32<C, BF16>(accM[pp], Am[a0 / 2], Em[a0 / 2], hi0[0], hi0[1], hi1[0], hi1[1]);
+      mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], lo0[0], lo0[1], hi0[0], hi0[1]);
+      mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], lo1[0], lo1[1], hi1[0], hi1[1]);
+    }
+  }
+  if constexpr (JJ + 2 < C::H + 2 * C::RY) sp_split_rows<C, BF16, SP, JJ + 2>(addr, Am, Em, Ac, Ec, accM, accC);
+}
+
+template <class C, bool BF16, int SP = C::SX>
 __device__ __forceinline__ void plane_sp_split(const float* row0, const uint4 (&Am)[C::RY + 1],
                                                const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
                                                const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
                                                float (&accC)[C::H / 2][4]) {
-#pragma unroll
-  for (int jj = 0; jj < C::H + 2 * C::RY; jj += 2) {
-    uint32_t hi0[2], lo0[2], hi1[2], lo1[2];
-    split4<C, BF16>(lds128(row0 + jj * C::SX), hi0, lo0);
-    split4<C, BF16>(lds128(row0 + (jj + 1) * C::SX), hi1, lo1);
-#pragma unroll
-    for (int pp = 0; pp < C::H / 2; ++pp) {
-      const int a0 = jj - 2 * pp;  // even; rows jj, jj+1 use A indices a0, a0+1
-      if (a0 >= 0 && a0 + 1 < C::NA) {
-        mma_k32<C, BF16>(accM[pp], Am[a0 / 2], Em[a0 / 2], hi0[0], hi0[1], hi1[0], hi1[1]);
-        mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], lo0[0], lo0[1], hi0[0], hi0[1]);
-        mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], lo1[0], lo1[1], hi1[0], hi1[1]);
-      }
-    }
-  }
+  sp_split_rows<C, BF16, SP, 0>(smem_u32(row0), Am, Em, Ac, Ec, accM, accC);
 }
 
 // --------------------------------------------------------------------------
@@ -291,15 +308,16 @@ __global__ void __launch_bounds__(C::kThreads)
         }
       }
       if (z < args.nz) {
+        float* o = args.dst + (z * args.ny + ybase) * args.nx + xbase + lane;
+        const int nx = (int)args.nx;
+        const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
+        const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
 #pragma unroll
         for (int yy = 0; yy < C::H; ++yy) {
-          const int64_t y = ybase + yy;
-          if (y < args.ny) {
+          if (yy < ylim) {
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int64_t x = xbase + lane + 32 * c;
-              if (x < args.nx) args.dst[(z * args.ny + y) * args.nx + x] = acc[yy][c];
-            }
+            for (int c = 0; c < 2; ++c)
+              if (lane + 32 * c < xlim) o[(size_t)yy * nx + 32 * c] = acc[yy][c];
           }
         }
       }
@@ -327,16 +345,30 @@ __global__ void __launch_bounds__(C::kThreads)
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
       }
       if (z < args.nz) {
+        float* o = args.dst + (z * args.ny + ybase) * args.nx + xbase + 16 * q + g;
+        const int nx = (int)args.nx;
+        if (ybase + C::H <= args.ny && xbase + 64 <= args.nx) {
+          // interior warp tile: no bounds checks
 #pragma unroll
-        for (int pp = 0; pp < C::H / 2; ++pp) {
+          for (int pp = 0; pp < C::H / 2; ++pp) {
 #pragma unroll
-          for (int sr = 0; sr < 2; ++sr) {
-            const int64_t y = ybase + 2 * pp + sr;
-            if (y < args.ny) {
+            for (int sr = 0; sr < 2; ++sr) {
+              float* orow = o + (size_t)(2 * pp + sr) * nx;
+              orow[0] = acc[pp][2 * sr];
+              orow[8] = acc[pp][2 * sr + 1];
+            }
+          }
+        } else {
+          const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
+          const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
 #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                const int64_t x = xbase + 16 * q + 8 * c + g;
-                if (x < args.nx) args.dst[(z * args.ny + y) * args.nx + x] = acc[pp][2 * sr + c];
+          for (int pp = 0; pp < C::H / 2; ++pp) {
+#pragma unroll
+            for (int sr = 0; sr < 2; ++sr) {
+              if (2 * pp + sr < ylim) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                  if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * nx + 8 * c] = acc[pp][2 * sr + c];
               }
             }
           }

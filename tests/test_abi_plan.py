@@ -80,7 +80,15 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     assert lib.spider_run(p.handle, ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), -1, None) == \
         _native.SPIDER_ERR_INVALID
     assert lib.spider_plan_set_steps_per_pass(p.handle, 0) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_plan_set_steps_per_pass(p.handle, 5) == _native.SPIDER_ERR_UNSUPPORTED
+    assert lib.spider_plan_set_steps_per_pass(p.handle, 3) == _native.SPIDER_OK
+    assert lib.spider_plan_set_tile_variant(p.handle, 3) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_plan_set_tile_variant(p.handle, 1) == _native.SPIDER_OK
+    assert lib.spider_plan_autotune(p.handle, None, None, 1, None, None, None) == _native.SPIDER_ERR_INVALID
     p.close()
+    p3 = spider.Plan(np.ones((3, 3, 3), np.float32), (8, 8, 8))
+    assert lib.spider_plan_set_steps_per_pass(p3.handle, 2) == _native.SPIDER_ERR_UNSUPPORTED
+    p3.close()
 
 
 # ------------------------------------------------------------------ operand decoding

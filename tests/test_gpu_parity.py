@@ -30,8 +30,11 @@ TOL = {
 ALL = list(TOL)
 
 
-def gpu_run(u0, w, steps, shape="box", prec="tf32", engine="sparse_tc"):
+def gpu_run(u0, w, steps, shape="box", prec="tf32", engine="sparse_tc", steps_per_pass=1, variant=0):
     plan = spider.Plan(w, u0.shape, shape, prec, engine)
+    if steps_per_pass > 1:
+        plan.set_steps_per_pass(steps_per_pass)
+    plan.set_tile_variant(variant)
     a = torch.from_numpy(np.ascontiguousarray(u0, np.float32)).cuda()
     b = torch.full_like(a, float("nan"))
     plan.run(a, b, steps)
@@ -193,3 +196,58 @@ def test_box2d_r3_8192_full_size_sampled(prec):
     tol = {"tf32": 2e-2, "f16x2": 1e-4, "bf16x3": 1e-3}[prec]
     assert np.all(np.abs(got - ref) <= tol * rms), (got, ref, rms)
     plan.close()
+
+
+@pytest.mark.parametrize("key", ALL)
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_fused_passes_match_single_steps(key, r):
+    # T steps per pass keep intermediate levels in FP32 shared memory with the
+    # zero halo re-applied, so every product and every rounding of T separate
+    # steps is repeated: bit-identical results.  One exception: the FP16/BF16
+    # splits add the hi*hi products of two input rows in one k32 MMA, and for
+    # odd r an intermediate level starts on an odd row, so an output row sits
+    # in the other half of the MMA and its products are grouped differently
+    # inside the tensor core; those results agree to the last bits only.
+    g = si.rng(11, r)
+    u0 = si.grid((300, 520), -1, 1, g)
+    w = si.normalised_coeffs(2, r, "box", g)
+    single = gpu_run(u0, w, 7, "box", key[1], key[0], 1)
+    ref = oracle.stencil(u0, w, 7)
+    exact = key[1] == "tf32" or r % 2 == 0
+    for T, variant in ((2, 0), (3, 1), (4, 2), (2, 1), (2, 2), (4, 1)):
+        fused = gpu_run(u0, w, 7, "box", key[1], key[0], T, variant)
+        if exact:
+            assert np.array_equal(fused, single), (key, r, T)
+        else:
+            check_close(fused, ref, key)
+            assert np.linalg.norm(fused - single) <= 1e-6 * np.linalg.norm(single), (key, r, T)
+
+
+@pytest.mark.parametrize("T", [2, 3, 4])
+def test_fused_parity_with_oracle(T):
+    u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
+    ref = oracle.stencil(u0, w, 9)
+    got = gpu_run(u0, w, 9, "box", "tf32", "sparse_tc", T)
+    check_close(got, ref, ("sparse_tc", "tf32"))
+    u1, w1 = si.workload_inputs(si.HEAT2D_512)
+    ref1 = oracle.stencil(u1, w1, 10)
+    got1 = gpu_run(u1, w1, 10, "star", "tf32", "sparse_tc", T)
+    check_close(got1, ref1, ("sparse_tc", "tf32"))
+
+
+def test_autotune_keeps_results_within_tolerance():
+    u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(512, 1024))
+    plan = spider.Plan(w, u0.shape, "box", "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    T, v = plan.autotune(a, b, 8)
+    assert 1 <= T <= 4 and v in (0, 1, 2)
+    plan.run(a, b, 8)
+    plan.sync()
+    ref = oracle.stencil(u0, w, 8)
+    check_close(b.cpu().numpy(), ref, ("sparse_tc", "tf32"))
+    # a second plan of the same kind takes the cached choice
+    p2 = spider.Plan(w, u0.shape, "box", "tf32")
+    assert p2.autotune(a, b, 8) == (T, v)
+    plan.close()
+    p2.close()
