@@ -40,7 +40,7 @@ WORKLOADS = {
     "heat3d": si.HEAT3D_512,
     "box3d": si.BOX3D_512,
 }
-DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60}
+DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60, "batched": 10, "serving": 40}
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 
@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spider", choices=["spider", "reference"])
-    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS) + ["batched", "serving"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
     ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--tile-variant", type=int, default=None)
     ap.add_argument("--extents", type=int, nargs="+", default=None,
                     help="override the grid size (same distributions; for profiling runs)")
+    ap.add_argument("--jobs", type=int, default=None, help="batched: use the first N of the 64 jobs")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -191,7 +192,7 @@ def run_reference(a):
     if rank != 0:
         return 0
     import oracle
-    wl = WORKLOADS[a.workload]
+    wl = WORKLOADS.get(a.workload, si.BOX2D_R3_8192)
     # each benchmark step is a bounded sample of the workload, sized so the
     # whole run (warm-up + timed) ends within about two minutes
     per_step_budget = 90.0 / (a.steps + a.warmup)
@@ -414,10 +415,129 @@ def run_spider(a):
     return 0
 
 
+def run_batched(a):
+    """64 2-D grids of mixed size, shape, radius and step count advanced by one
+    spider_batch call (one persistent launch over a tile queue, issued as a CUDA
+    graph); compared with the same jobs run one spider_run after another."""
+    import torch
+    import paper_2506_22035_gb300 as spider
+    from paper_2506_22035_gb300 import build as _b
+    _b.build()
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    jobs = si.batched_jobs()[: a.jobs] if a.jobs else si.batched_jobs()
+    plans, ins, outs = [], [], []
+    work = 0
+    for jb in jobs:
+        u0, w = si.job_inputs(jb)
+        plans.append(spider.Plan(w, jb.extents, jb.shape, "tf32"))
+        ins.append(torch.from_numpy(u0).to(dev))
+        outs.append(torch.empty_like(ins[-1]))
+        work += int(np.prod(jb.extents)) * jb.steps
+    steps = [jb.steps for jb in jobs]
+    for _ in range(a.warmup):
+        spider.batch(plans, ins, outs, steps, stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        spider.batch(plans, ins, outs, steps, stream)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    # the same jobs one after another through spider_run (each plan tuned)
+    for p, x, y, n in zip(plans, ins, outs, steps):
+        p.autotune(x, y, n, stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for _ in range(max(1, a.steps // 2)):
+        for p, x, y, n in zip(plans, ins, outs, steps):
+            p.run(x, y, n, stream)
+    torch.cuda.synchronize(dev)
+    dt_seq = (time.perf_counter() - t1) / max(1, a.steps // 2)
+    line = {"metric": "GStencil/s", "value": world * work * a.steps / dt / 1e9, "unit": "GStencil/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+            "data": "synthetic",
+            "config": {"workload": "batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, "
+                                   "10-200 steps", "stencil_updates_per_step": work, "engine": "sparse_tc",
+                       "launch": "spider_batch (persistent tile queue, CUDA graph)"},
+            "sequential_spider_run": {"value": work / dt_seq / 1e9, "unit": "GStencil/s",
+                                      "note": "same jobs, one autotuned spider_run after another"}}
+    for p in plans:
+        p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(a):
+    """Poisson arrivals (200 jobs/s) of mixed 2-D/3-D stencil jobs submitted to
+    the continuous-batching server; a bounded prefix of the arrival sequence
+    (its total work is ~1e5 times a GPU-second budget otherwise)."""
+    import torch
+    import paper_2506_22035_gb300 as spider
+    from paper_2506_22035_gb300 import build as _b
+    _b.build()
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    arrivals = si.serving_arrivals()
+    chosen, work = [], 0
+    for jb in arrivals:
+        wk = int(np.prod(jb.extents)) * jb.steps
+        if work + wk > 3.0e10 and chosen:
+            continue
+        chosen.append(jb)
+        work += wk
+        if len(chosen) >= a.steps:
+            break
+    inputs = [si.job_inputs(jb) for jb in chosen]
+    server = spider.Server(120 * 10**9)
+    plans = [spider.Plan(w, jb.extents, jb.shape, "tf32") for jb, (u0, w) in zip(chosen, inputs)]
+    t0 = time.perf_counter()
+    tickets = []
+    base = chosen[0].arrival_s
+    for jb, p, (u0, w) in zip(chosen, plans, inputs):
+        while time.perf_counter() - t0 < jb.arrival_s - base:
+            time.sleep(0.0002)
+        tickets.append(server.submit(p, u0, jb.steps, jb.err_target))
+    lat = {}
+    outs = {t: np.empty_like(u0) for t, (u0, w) in zip(tickets, inputs)}
+    while len(lat) < len(tickets):
+        for t in tickets:
+            if t not in lat:
+                done, l = server.poll(t, outs[t])
+                if done:
+                    lat[t] = l
+        time.sleep(0.001)
+    dt = time.perf_counter() - t0
+    server.close()
+    for p in plans:
+        p.close()
+    ls = np.array(sorted(lat.values()))
+    span = chosen[-1].arrival_s - base if len(chosen) > 1 else 0.0
+    line = {"metric": "GStencil/s", "value": work / dt / 1e9, "unit": "GStencil/s", "n_gpus": world,
+            "steps": len(chosen), "warmup": 0, "ms_per_step": dt / len(chosen) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f16x2", "data": "synthetic",
+            "config": {"workload": "serving: Poisson 200/s, 2-D side 256-8192 / 3-D side 64-512, r 1-3, "
+                                   "10-500 steps, error target 1e-3 (TF32) or 1e-5 (FP16 hi/lo)",
+                       "jobs": len(chosen), "stencil_updates": work, "hbm_budget_bytes": 120 * 10**9},
+            "latency_s": {"p50": float(np.percentile(ls, 50)), "p99": float(np.percentile(ls, 99)),
+                          "max": float(ls[-1])},
+            "offered_load_gstencil_s": work / max(span, 1e-9) / 1e9 if span > 0 else None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return run_batched(a)
+    if a.workload == "serving":
+        return run_serving(a)
     return run_spider(a)
 
 

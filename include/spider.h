@@ -182,10 +182,15 @@ spider_status spider_plan_sync(spider_plan plan, cudaStream_t stream);
 void spider_plan_destroy(spider_plan plan);
 
 /* spider_batch -- advances n independent grids in one persistent launch.
- * plans[i], ins[i], outs[i], steps[i] as for spider_run; every plan must be
- * SPARSE_TC.  Work items (grid, tile, step) are taken from a device queue;
- * step t+1 of a grid starts on a tile only after step t finished on the
- * neighbouring tiles (per-grid counters with bounded waits).  n <= 4096. */
+ * plans[i], ins[i], outs[i], steps[i] as for spider_run (a plan may appear
+ * once).  2-D grids with TF32 sparse plans go through one persistent kernel,
+ * issued as a CUDA graph: work items (time step, grid, 64 x 128 tile) are
+ * claimed from a device queue in step-major order, and step s of a tile
+ * starts only after the tile and its eight neighbours finished step s-1
+ * (per-tile counters, bounded waits).  Other plans (3-D, split precisions,
+ * comparator engines) run through spider_run on the same stream after it.
+ * Synchronous: returns when all grids are done.  n <= 4096.
+ * SPIDER_ERR_TIMEOUT if a dependency wait ran out. */
 spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                            const int64_t* steps, cudaStream_t stream);
 

@@ -153,5 +153,43 @@ def batch(plans, ins, outs, steps, stream=None) -> None:
     check(_native.load().spider_batch(n, P, I, O, S, _stream_handle(stream)), "spider_batch")
 
 
-__all__ = ["Plan", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
+class Server:
+    """Continuous-batching stencil server (spider_server_create / submit / poll)."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        h = ctypes.c_void_p()
+        check(_native.load().spider_server_create(int(hbm_budget_bytes), ctypes.byref(h)), "spider_server_create")
+        self._h = h
+
+    def submit(self, plan: Plan, host_in: np.ndarray, steps: int, err_target: float = 1e-3) -> int:
+        src = np.ascontiguousarray(host_in, dtype=np.float32)
+        if src.size != plan.points:
+            raise ValueError("host grid has the wrong size")
+        t = ctypes.c_uint64()
+        check(_native.load().spider_submit(self._h, plan.handle, src.ctypes.data_as(ctypes.c_void_p), int(steps),
+                                           float(err_target), ctypes.byref(t)), "spider_submit")
+        return t.value
+
+    def poll(self, ticket: int, out: np.ndarray | None = None):
+        """(done, latency_s); when done and `out` is given, the result is copied
+        into it and the ticket is released."""
+        done, lat = ctypes.c_int(), ctypes.c_double()
+        ptr = out.ctypes.data_as(ctypes.c_void_p) if out is not None else None
+        check(_native.load().spider_poll(self._h, ctypes.c_uint64(ticket), ptr, ctypes.byref(done),
+                                         ctypes.byref(lat)), "spider_poll")
+        return bool(done.value), lat.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _native.load().spider_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["Plan", "Server", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
            "PRECISIONS", "ENGINES", "SHAPES"]

@@ -90,6 +90,12 @@ static spider_status ensure_scratch(spider_plan_t* p) {
   return SPIDER_OK;
 }
 
+spider_status ensure_plan_device(spider_plan_t* p, bool scratch) {
+  spider_status s = ensure_device(p);
+  if (s != SPIDER_OK || !scratch) return s;
+  return ensure_scratch(p);
+}
+
 static bool overlaps(const void* a, const void* b, size_t bytes) {
   const char* x = static_cast<const char*>(a);
   const char* y = static_cast<const char*>(b);

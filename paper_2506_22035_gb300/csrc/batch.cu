@@ -1,0 +1,454 @@
+// spider_batch: many 2-D grids of different sizes, radii and step counts in
+// one persistent launch over a device work queue.
+//
+// Work items are (time step s, job, tile) in step-major order; CTAs claim them
+// with one atomic counter.  Item (s, j, tile) reads job j's grid of step s
+// over the tile plus its halo, so it may start only after the tile and its
+// eight neighbours have finished step s-1 (those are also the last readers of
+// the buffer it overwrites).  Each job keeps one completion counter per tile;
+// a CTA waits on its neighbours' counters with bounded spins (acquire loads)
+// and publishes its own with a release store after a device-scope fence.
+// Because items are claimed in global order and an item only waits on items
+// of an earlier step, every awaited item is already held by a running CTA:
+// the queue cannot deadlock, whatever the residency.
+//
+// The tile computation is the one-step SPIDER tile of stencil_step_kernel
+// (TF32 sparse MMA, 64 x 128 outputs, TMA halo box).  Each job brings its own
+// tensor maps and packed operands.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "stencil_kernels.cuh"
+
+namespace spider {
+namespace {
+
+constexpr int kBY = 64, kBX = 128, kWarpsY = 4, kWarpsX = 2, kH = 16;
+constexpr int kThreads = kWarpsY * kWarpsX * 32;
+constexpr int kMaxStageFloats = (kBY + 2 * kMaxR) * (kBX + 2 * kHaloX);
+constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
+constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
+constexpr int kMaxTableSmem = 48 * 1024;
+
+struct BatchJob {
+  int64_t nx, ny;
+  int r;
+  int tiles_x, tiles_y;
+  int steps;
+  int first;           // parity of the first destination (last step lands in out)
+  int map0;            // tensor maps: map0 + 0 = in, + 1 = out, + 2 = scratch
+  const uint4* a;      // packed A operands (TF32, per A index)
+  const uint32_t* meta;
+  float* bufs[2];      // out, scratch
+  const float* in;
+  int* done;           // per-tile count of completed steps
+  int tma;             // 1: rows and buffers TMA-describable; 0: consumers load the halo box
+};
+
+template <int R>
+using BatchTile = TileCfg<0, R, R, 1, kWarpsY, kWarpsX, kH>;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One tile of one step: operands to registers, MMAs, write-back.
+template <int R>
+__device__ __forceinline__ void batch_tile(const BatchJob& jb, const float* S, float* dst, int x0, int y0) {
+  using C = BatchTile<R>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int wx = warp % C::WX, wy = warp / C::WX;
+  uint4 A[C::NA];
+  uint32_t E[C::NA];
+#pragma unroll
+  for (int a = 0; a < C::NA; ++a) {
+    A[a] = jb.a[(size_t)a * 32 + lane];
+    E[a] = jb.meta[(size_t)a * 32 + lane];
+  }
+  float acc[C::H / 2][4];
+#pragma unroll
+  for (int i = 0; i < C::H / 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  const float* row0 = S + (size_t)(wy * C::H) * C::SX + wx * 64 + 8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
+  plane_sp_tf32<C>(row0, A, E, acc);
+  const int ybase = y0 + wy * C::H, xbase = x0 + wx * 64;
+  float* o = dst + (int64_t)ybase * jb.nx + xbase + 16 * q + g;
+  const int ylim = (int)(jb.ny - ybase < C::H ? jb.ny - ybase : C::H);
+  const int xlim = (int)(jb.nx - xbase < 64 ? jb.nx - xbase : 64);
+#pragma unroll
+  for (int pp = 0; pp < C::H / 2; ++pp)
+#pragma unroll
+    for (int sr = 0; sr < 2; ++sr)
+      if (2 * pp + sr < ylim) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * jb.nx + 8 * c] = acc[pp][2 * sr + c];
+      }
+}
+
+// Warp-parallel search: the largest index i in [0, n) with table[i] <= key
+// (table ascending, table[0] <= key).  32 probes per round.
+__device__ __forceinline__ int warp_search(const long long* __restrict__ table, int n, long long key, int lane) {
+  int lo = 0, len = n;
+  while (len > 1) {
+    const int step = (len + 31) / 32;
+    const int idx = lo + lane * step;
+    const bool ok = idx < lo + len && idx < n && table[idx] <= key;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const int best = 31 - __clz(m);  // lane 0 always qualifies
+    lo = lo + best * step;
+    len = min(step, n - lo);
+  }
+  return lo;
+}
+
+struct ItemSlot {
+  int job, s, tile, end;
+};
+
+// kThreads consumer threads (8 warps) compute tiles; one extra producer warp
+// claims items, waits for their dependencies and issues their TMA loads into
+// a two-stage ring, so the queue latency overlaps the tensor-core work.
+// The queue tables (job records, job order, step offsets, jobs active per
+// step, tile prefix sums) are one contiguous block `tables` of `tables_bytes`
+// bytes whose parts start at the given offsets.  When `tables_in_smem` is set
+// the CTA copies the block into shared memory first, so claiming and decoding
+// an item costs one global atomic and no other global round trip.
+__global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned char* __restrict__ tables,
+                                                             int tables_bytes, int tables_in_smem, int o_order,
+                                                             int o_step, int o_active, int o_tp,
+                                                             const CUtensorMap* __restrict__ maps, int max_steps,
+                                                             int* __restrict__ counter, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base_u32 = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kStageStride);
+  uint64_t* empty = full + 2;
+  ItemSlot* slot = reinterpret_cast<ItemSlot*>(empty + 2);
+  unsigned char* tsm = smem + 2 * kStageStride + 128;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tables_in_smem) {
+    const uint4* src = reinterpret_cast<const uint4*>(tables);
+    uint4* dstv = reinterpret_cast<uint4*>(tsm);
+    for (int i = tid; i < tables_bytes / 16; i += blockDim.x) dstv[i] = src[i];
+  }
+  const unsigned char* tb = tables_in_smem ? tsm : tables;
+  const BatchJob* __restrict__ jobs = reinterpret_cast<const BatchJob*>(tb);
+  const int* __restrict__ order = reinterpret_cast<const int*>(tb + o_order);
+  const long long* __restrict__ step_off = reinterpret_cast<const long long*>(tb + o_step);
+  const int* __restrict__ active = reinterpret_cast<const int*>(tb + o_active);
+  const long long* __restrict__ tile_prefix = reinterpret_cast<const long long*>(tb + o_tp);
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long total = step_off[max_steps];
+
+  if (warp == kThreads / 32) {
+    // ---------------- producer warp ----------------
+    for (long long k = 0;; ++k) {
+      const int st = (int)(k & 1);
+      const long long use = k >> 1;
+      long long item = 0;
+      if (lane == 0) item = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ULL);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      // the stage must have been released by the consumers (use - 1)
+      if (use > 0) {
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), status);
+        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+      }
+      if (item >= total) {
+        if (lane == 0) {
+          slot[st].end = 1;
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+        }
+        break;
+      }
+      const int s = warp_search(step_off, max_steps, item, lane);
+      const long long local = item - step_off[s];
+      const int kk = warp_search(tile_prefix, active[s], local, lane);
+      const int j = order[kk];
+      const BatchJob& jb = jobs[j];
+      const int tile = (int)(local - tile_prefix[kk]);
+      const int tx = tile % jb.tiles_x, ty = tile / jb.tiles_x;
+      // lanes 0..8 each wait for one tile of the 3 x 3 neighbourhood (step s-1)
+      if (s > 0 && lane < 9) {
+        const int ntx = tx + lane % 3 - 1, nty = ty + lane / 3 - 1;
+        if (ntx >= 0 && nty >= 0 && ntx < jb.tiles_x && nty < jb.tiles_y) {
+          const int* flag = jb.done + nty * jb.tiles_x + ntx;
+          if (ld_acquire(flag) < s) {
+            const long long t0 = clock64();
+            while (ld_acquire(flag) < s) {
+              if (clock64() - t0 > kWaitCycles) { atomicExch(status, kStatusTimeout); break; }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        slot[st].job = j;
+        slot[st].s = s;
+        slot[st].tile = tile;
+        slot[st].end = 0;
+        if (jb.tma) {
+          // the neighbours' generic-proxy stores must be visible to the TMA read
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          const int src_map = jb.map0 + (s == 0 ? 0 : 1 + (jb.first + s - 1) % 2);
+          const uint32_t bytes = (uint32_t)((kBY + 2 * jb.r) * (kBX + 2 * kHaloX) * 4);
+          mbar_arrive_expect_tx(&full[st], bytes);
+          tma_load_3d(smem + st * kStageStride, &maps[src_map], &full[st], tx * kBX - kHaloX, ty * kBY - jb.r, 0);
+        } else {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+        }
+      }
+      __syncwarp();
+    }
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
+  for (long long k = 0;; ++k) {
+    const int st = (int)(k & 1);
+    const bool landed = mbar_wait_bounded(&full[st], (uint32_t)((k >> 1) & 1), status);
+    if (!landed) break;
+    const ItemSlot it = slot[st];
+    if (it.end) break;
+    const BatchJob& jb = jobs[it.job];
+    const int tx = it.tile % jb.tiles_x, ty = it.tile / jb.tiles_x;
+    float* Sw = reinterpret_cast<float*>(smem + st * kStageStride);
+    if (!jb.tma) {
+      const float* src = it.s == 0 ? jb.in : jb.bufs[(jb.first + it.s - 1) % 2];
+      load_box_async(src, jb.nx, jb.ny, 1, (int64_t)tx * kBX - kHaloX, (int64_t)ty * kBY - jb.r, 0,
+                     kBX + 2 * kHaloX, kBY + 2 * jb.r, 1, Sw, warp, kThreads / 32, lane);
+      asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+    }
+    const float* S = Sw;
+    float* dst = jb.bufs[(jb.first + it.s) % 2];
+    switch (jb.r) {
+      case 1: batch_tile<1>(jb, S, dst, tx * kBX, ty * kBY); break;
+      case 2: batch_tile<2>(jb, S, dst, tx * kBX, ty * kBY); break;
+      default: batch_tile<3>(jb, S, dst, tx * kBX, ty * kBY); break;
+    }
+    // all consumer stores of this tile, then one GPU-scope release of the
+    // tile's step counter (the barrier orders the other threads' stores
+    // before thread 0's release)
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // consumers only
+    if (tid == 0) {
+      st_release(jb.done + it.tile, it.s + 1);
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+    }
+  }
+}
+
+}  // namespace
+}  // namespace spider
+
+using namespace spider;
+
+extern "C" spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
+                                      const int64_t* steps, cudaStream_t stream) {
+  set_error("");
+  if (n < 0 || n > 4096) return fail(SPIDER_ERR_INVALID, "n must be in [0, 4096]");
+  if (n == 0) return SPIDER_OK;
+  if (!plans || !ins || !outs || !steps) return fail(SPIDER_ERR_INVALID, "NULL array");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !ins[i] || !outs[i] || steps[i] < 0) return fail(SPIDER_ERR_INVALID, "bad job");
+    const size_t bytes = (size_t)plans[i]->points() * 4;
+    const char* a = reinterpret_cast<const char*>(ins[i]);
+    const char* b = reinterpret_cast<const char*>(outs[i]);
+    if (a < b + bytes && b < a + bytes) return fail(SPIDER_ERR_INVALID, "grid_out overlaps grid_in");
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) return fail(SPIDER_ERR_INVALID, "a plan may appear once per batch (its scratch grid)");
+  }
+  // Jobs the persistent queue handles: 2-D sparse TF32 with TMA-describable
+  // rows and at least one step.  Others run through their own plan, on the
+  // same stream, after the persistent launch.
+  std::vector<int> queued, direct;
+  for (int i = 0; i < n; ++i) {
+    spider_plan_t* p = plans[i];
+    const bool ok = p->ndim == 2 && p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec == SPIDER_TF32 && steps[i] > 0;
+    (ok ? queued : direct).push_back(i);
+  }
+  if (!queued.empty()) {
+    const int nq = (int)queued.size();
+    std::vector<BatchJob> jobs(nq);
+    std::vector<CUtensorMap> maps(3 * (size_t)nq);
+    std::vector<long long> tiles(nq);
+    long long total_tiles = 0;
+    int max_steps = 0;
+    for (int k = 0; k < nq; ++k) {
+      const int i = queued[k];
+      spider_plan_t* p = plans[i];
+      std::lock_guard<std::mutex> lock(p->mu);
+      spider_status st = ensure_plan_device(p, steps[i] > 1);
+      if (st != SPIDER_OK) return st;
+      BatchJob& jb = jobs[k];
+      jb.nx = p->nx;
+      jb.ny = p->ny;
+      jb.r = p->r;
+      jb.tiles_x = (int)((p->nx + kBX - 1) / kBX);
+      jb.tiles_y = (int)((p->ny + kBY - 1) / kBY);
+      jb.steps = (int)steps[i];
+      jb.first = (steps[i] % 2 == 1) ? 0 : 1;
+      jb.map0 = 3 * k;
+      jb.a = reinterpret_cast<const uint4*>(p->dev.a_words);
+      jb.meta = p->dev.meta_words;
+      jb.bufs[0] = outs[i];
+      jb.bufs[1] = p->dev.scratch;
+      jb.in = ins[i];
+      jb.done = nullptr;
+      jb.tma = 1;
+      const float* bases[3] = {ins[i], outs[i], p->dev.scratch};
+      for (int m = 0; m < 3; ++m) {
+        std::memset(&maps[3 * k + m], 0, sizeof(CUtensorMap));
+        if (bases[m] == nullptr) { maps[3 * k + m] = maps[3 * k]; continue; }  // no scratch for 1-step jobs
+        if (!make_tensor_map(&maps[3 * k + m], bases[m], p->nx, p->ny, 1, kBX + 2 * kHaloX, kBY + 2 * p->r, 1))
+          jb.tma = 0;  // rows not 16-byte aligned: consumers load the box
+      }
+      tiles[k] = (long long)jb.tiles_x * jb.tiles_y;
+      total_tiles += tiles[k];
+      max_steps = std::max(max_steps, jb.steps);
+    }
+    // order jobs by descending step count: the jobs active at step s are a prefix
+    std::vector<int> order(nq);
+    for (int k = 0; k < nq; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].steps > jobs[b].steps; });
+    std::vector<long long> tile_prefix(nq + 1, 0);
+    for (int k = 0; k < nq; ++k) tile_prefix[k + 1] = tile_prefix[k] + tiles[order[k]];
+    std::vector<int> active(max_steps);
+    std::vector<long long> step_off(max_steps + 1, 0);
+    for (int s = 0; s < max_steps; ++s) {
+      int c = 0;
+      while (c < nq && jobs[order[c]].steps > s) ++c;
+      active[s] = c;
+      step_off[s + 1] = step_off[s] + tile_prefix[c];
+    }
+    // one device block: [tables: jobs | order | step_off | active | tile_prefix] | maps | done | counter | status
+    auto align = [](size_t x) { return (x + 127) / 128 * 128; };
+    const size_t o_jobs = 0;
+    const size_t o_order = align(o_jobs + sizeof(BatchJob) * nq);
+    const size_t o_step = align(o_order + sizeof(int) * nq);
+    const size_t o_active = align(o_step + sizeof(long long) * (max_steps + 1));
+    const size_t o_tp = align(o_active + sizeof(int) * max_steps);
+    const size_t tables_bytes = align(o_tp + sizeof(long long) * (nq + 1));
+    const size_t o_maps = tables_bytes;
+    const size_t o_done = align(o_maps + sizeof(CUtensorMap) * maps.size());
+    const size_t o_ctr = align(o_done + sizeof(int) * total_tiles);
+    const size_t o_status = o_ctr + 16;
+    const size_t bytes = align(o_status + 16);
+    const int tables_in_smem = tables_bytes <= (size_t)kMaxTableSmem ? 1 : 0;
+    const int smem_bytes = kSmemBase + (tables_in_smem ? (int)tables_bytes : 0);
+    // the queue buffer is kept between calls (per device) and grown on demand
+    static std::mutex qmu;
+    static unsigned char* qbuf[64] = {nullptr};
+    static size_t qcap[64] = {0};
+    std::lock_guard<std::mutex> qlock(qmu);
+    int devid = 0;
+    cudaGetDevice(&devid);
+    if (devid < 0 || devid >= 64) return fail(SPIDER_ERR_UNSUPPORTED, "device index out of range");
+    cudaError_t e = cudaSuccess;
+    if (qcap[devid] < bytes) {
+      e = cudaStreamSynchronize(stream);  // the old buffer may still be in use on this stream
+      if (e == cudaSuccess && qbuf[devid]) cudaFree(qbuf[devid]);
+      qbuf[devid] = nullptr;
+      qcap[devid] = 0;
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&qbuf[devid]), bytes * 2);
+      if (e != cudaSuccess) { cudaGetLastError(); return fail(SPIDER_ERR_OOM, "batch work queue"); }
+      qcap[devid] = bytes * 2;
+    }
+    unsigned char* dev = qbuf[devid];
+    long long done_off = 0;
+    for (int k = 0; k < nq; ++k) {
+      jobs[k].done = reinterpret_cast<int*>(dev + o_done) + done_off;
+      done_off += tiles[k];
+    }
+    std::vector<unsigned char> host(bytes, 0);  // zero counters and status
+    std::memcpy(host.data() + o_jobs, jobs.data(), sizeof(BatchJob) * nq);
+    std::memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+    std::memcpy(host.data() + o_order, order.data(), sizeof(int) * nq);
+    std::memcpy(host.data() + o_active, active.data(), sizeof(int) * max_steps);
+    std::memcpy(host.data() + o_step, step_off.data(), sizeof(long long) * (max_steps + 1));
+    std::memcpy(host.data() + o_tp, tile_prefix.data(), sizeof(long long) * (nq + 1));
+    e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host image is freed on return
+    if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, "batch work queue upload");
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+      attr_err = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmemBase + kMaxTableSmem);
+    });
+    if (attr_err != cudaSuccess) return fail(SPIDER_ERR_CUDA, "batch kernel attributes");
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads + 32, smem_bytes);
+    const long long total_items = step_off[max_steps];
+    const int grid = (int)std::max<long long>(
+        1, std::min<long long>(total_items, (long long)std::max(occ, 1) * device_sm_count()));
+    // The persistent launch is issued as a CUDA graph: the work-queue reset
+    // (counter and per-tile step counters) and the kernel, launched on the
+    // caller's stream.
+    const unsigned char* a_tables = dev;
+    int a_tbytes = (int)tables_bytes, a_tsm = tables_in_smem, a_oo = (int)o_order, a_os = (int)o_step,
+        a_oa = (int)o_active, a_ot = (int)o_tp;
+    const CUtensorMap* a_maps = reinterpret_cast<const CUtensorMap*>(dev + o_maps);
+    int a_max = max_steps;
+    int* a_ctr = reinterpret_cast<int*>(dev + o_ctr);
+    int* a_status = reinterpret_cast<int*>(dev + o_status);
+    void* kargs[] = {(void*)&a_tables, (void*)&a_tbytes, (void*)&a_tsm, (void*)&a_oo, (void*)&a_os, (void*)&a_oa,
+                     (void*)&a_ot, (void*)&a_maps, (void*)&a_max, (void*)&a_ctr, (void*)&a_status};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphCreate(&graph, 0);
+    cudaGraphNode_t reset = nullptr, kern = nullptr;
+    if (e == cudaSuccess) {
+      cudaMemsetParams mp = {};
+      mp.dst = dev + o_done;
+      mp.value = 0;
+      mp.elementSize = 1;
+      mp.width = bytes - o_done;
+      mp.height = 1;
+      mp.pitch = 0;
+      e = cudaGraphAddMemsetNode(&reset, graph, nullptr, 0, &mp);
+    }
+    if (e == cudaSuccess) {
+      cudaKernelNodeParams kp = {};
+      kp.func = reinterpret_cast<void*>(batch_kernel);
+      kp.gridDim = dim3(grid);
+      kp.blockDim = dim3(kThreads + 32);
+      kp.sharedMemBytes = smem_bytes;
+      kp.kernelParams = kargs;
+      e = cudaGraphAddKernelNode(&kern, graph, &reset, 1, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, stream);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, a_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    if (status != 0) return fail(SPIDER_ERR_TIMEOUT, "a dependency wait in the batch queue ran out");
+  }
+  for (int i : direct) {
+    std::lock_guard<std::mutex> lock(plans[i]->mu);
+    spider_status s = run_device(plans[i], ins[i], outs[i], steps[i], stream);
+    if (s != SPIDER_OK) return s;
+  }
+  return SPIDER_OK;
+}

@@ -98,6 +98,38 @@ __device__ __forceinline__ float4 lds128_at(uint32_t addr) {
   return v;
 }
 
+// Asynchronous 4-byte global -> shared copy; src_bytes = 0 writes a zero
+// (the source address is then not read, but it is kept inside the grid).
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Loads the box of SZ x SY x SX floats whose first element is grid point
+// (z0, y0, x0) into shared memory (row pitch SX), zero outside the
+// nz x ny x nx grid, for grids whose rows TMA cannot describe.  Rows are
+// spread over the warps, columns over the lanes (coalesced); every thread
+// keeps many copies in flight.  The caller waits with a barrier afterwards.
+__device__ __forceinline__ void load_box_async(const float* __restrict__ src, int64_t nx, int64_t ny, int64_t nz,
+                                               int64_t x0, int64_t y0, int64_t z0, int SX, int SY, int SZ, float* S,
+                                               int warp, int nwarps, int lane) {
+  for (int row = warp; row < SY * SZ; row += nwarps) {
+    const int zz = row / SY, yy = row - zz * SY;
+    const int64_t gz = z0 + zz, gy = y0 + yy;
+    const bool row_ok = gz >= 0 && gz < nz && gy >= 0 && gy < ny;
+    const float* srow = src + (row_ok ? (gz * ny + gy) * nx : 0);
+    float* drow = S + row * SX;
+    for (int xx = lane; xx < SX; xx += 32) {
+      const int64_t gx = x0 + xx;
+      const bool ok = row_ok && gx >= 0 && gx < nx;
+      cp_async4(drow + xx, ok ? srow + gx : src, ok);
+    }
+  }
+  cp_async_wait_all();
+}
+
 __device__ __forceinline__ uint32_t cvt_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));

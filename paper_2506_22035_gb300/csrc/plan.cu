@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
+#include <vector>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -97,8 +98,56 @@ struct WindowMatrix {
   bool mask[16][16];
 };
 
-// A_a for plane dz (index dzi = dz + rz) in window coordinates.
-WindowMatrix window_matrix(const spider_plan_t* p, int dzi, int a, Part part) {
+// TF32 coefficients rounded so that their sum stays as close as possible to
+// the sum of the FP32 coefficients.  Each weight takes one of its two TF32
+// neighbours: round to nearest first, then flip the weights whose flip best
+// reduces the error of the sum.  With round-to-nearest alone the rounding
+// errors of the weights add up to a systematic error of the stencil's
+// response to the constant mode that grows linearly with the number of steps;
+// here it is bounded by the spacing of the smallest weights.  Exactly
+// representable weights are unchanged.
+std::vector<float> tf32_sum_preserving(const std::vector<float>& w) {
+  const size_t n = w.size();
+  std::vector<float> out(n), other(n);
+  double resid = 0;
+  for (size_t i = 0; i < n; ++i) {
+    out[i] = tf32_value(w[i]);
+    uint32_t u;
+    std::memcpy(&u, &w[i], 4);
+    const uint32_t t = u & 0xFFFFE000u;  // neighbour toward zero
+    float lo, hi;
+    std::memcpy(&lo, &t, 4);
+    const uint32_t t2 = t + 0x2000u;     // neighbour away from zero
+    std::memcpy(&hi, &t2, 4);
+    other[i] = (lo == w[i]) ? w[i] : (out[i] == lo ? hi : lo);
+    resid += (double)w[i] - (double)out[i];
+  }
+  std::vector<bool> flipped(n, false);
+  for (;;) {
+    int best = -1;
+    double best_abs = std::fabs(resid), best_cost = 0;
+    for (size_t i = 0; i < n; ++i) {
+      if (flipped[i] || other[i] == out[i]) continue;
+      const double delta = (double)other[i] - (double)out[i];
+      const double r2 = std::fabs(resid - delta);
+      const double cost = std::fabs((double)w[i] - (double)other[i]);
+      if (r2 < best_abs || (best >= 0 && r2 == best_abs && cost < best_cost)) {
+        best = (int)i;
+        best_abs = r2;
+        best_cost = cost;
+      }
+    }
+    if (best < 0) break;
+    resid -= (double)other[best] - (double)out[best];
+    std::swap(out[best], other[best]);
+    flipped[best] = true;
+  }
+  return out;
+}
+
+// A_a for plane dz (index dzi = dz + rz) in window coordinates; `coeffs`
+// supplies the cube (the plan's FP32 weights or their TF32 rounding).
+WindowMatrix window_matrix(const spider_plan_t* p, const std::vector<float>& coeffs, int dzi, int a, Part part) {
   WindowMatrix A;
   const int wy = 2 * p->ry + 1, wx = 2 * p->rx + 1;
   for (int m = 0; m < 16; ++m) {
@@ -108,7 +157,7 @@ WindowMatrix window_matrix(const spider_plan_t* p, int dzi, int a, Part part) {
       const int dx = q - kHaloX - xo;
       const bool in = (dy >= -p->ry && dy <= p->ry && dx >= -p->rx && dx <= p->rx);
       A.mask[m][q] = in;
-      A.v[m][q] = in ? part_value(p->w[((size_t)dzi * wy + (dy + p->ry)) * wx + (dx + p->rx)], part) : 0.f;
+      A.v[m][q] = in ? part_value(coeffs[((size_t)dzi * wy + (dy + p->ry)) * wx + (dx + p->rx)], part) : 0.f;
     }
   }
   return A;
@@ -235,6 +284,7 @@ spider_status build_operands(spider_plan_t* p) {
   p->a_words.clear();
   p->meta_words.clear();
   try {
+    const std::vector<float> w_tf32 = tf32_sum_preserving(p->w);
     if (p->engine == SPIDER_ENGINE_CUDA_CORE) {
       p->n_combos = 0;
       return SPIDER_OK;
@@ -244,7 +294,7 @@ spider_status build_operands(spider_plan_t* p) {
       p->a_words.resize((size_t)p->n_arows * 32 * 8);
       for (int dzi = 0; dzi < planes; ++dzi)
         for (int a = 0; a < na; ++a)
-          pack_tf32_dense(window_matrix(p, dzi, a, Part::TF32), &p->a_words[((size_t)dzi * na + a) * 256]);
+          pack_tf32_dense(window_matrix(p, w_tf32, dzi, a, Part::Full), &p->a_words[((size_t)dzi * na + a) * 256]);
       return SPIDER_OK;
     }
     const int cpp = combos_per_plane(p->prec, p->ry);
@@ -255,7 +305,7 @@ spider_status build_operands(spider_plan_t* p) {
       if (p->prec == SPIDER_TF32 || p->prec == SPIDER_AUTO) {
         for (int a = 0; a < na; ++a) {
           const size_t c = (size_t)dzi * cpp + a;
-          pack_tf32_sparse(window_matrix(p, dzi, a, Part::TF32), &p->a_words[c * 128], &p->meta_words[c * 32]);
+          pack_tf32_sparse(window_matrix(p, w_tf32, dzi, a, Part::Full), &p->a_words[c * 128], &p->meta_words[c * 32]);
         }
       } else {
         const bool bf = p->prec == SPIDER_BF16X3;
@@ -264,13 +314,13 @@ spider_status build_operands(spider_plan_t* p) {
         // main combos: [K_hi(2c) | K_hi(2c+1)] times [X_hi(j); X_hi(j+1)]
         for (int c = 0; c <= p->ry; ++c) {
           const size_t ci = (size_t)dzi * cpp + c;
-          pack_16bit_sparse_k32(window_matrix(p, dzi, 2 * c, hi), window_matrix(p, dzi, 2 * c + 1, hi), bf,
+          pack_16bit_sparse_k32(window_matrix(p, p->w, dzi, 2 * c, hi), window_matrix(p, p->w, dzi, 2 * c + 1, hi), bf,
                                 &p->a_words[ci * 128], &p->meta_words[ci * 32]);
         }
         // correction combos: [K_hi(a) | K_lo(a)] times [X_lo(j); X_hi(j)]
         for (int a = 0; a < na; ++a) {
           const size_t ci = (size_t)dzi * cpp + (p->ry + 1) + a;
-          pack_16bit_sparse_k32(window_matrix(p, dzi, a, hi), window_matrix(p, dzi, a, lo), bf,
+          pack_16bit_sparse_k32(window_matrix(p, p->w, dzi, a, hi), window_matrix(p, p->w, dzi, a, lo), bf,
                                 &p->a_words[ci * 128], &p->meta_words[ci * 32]);
         }
       }

@@ -98,5 +98,7 @@ int combos_per_plane(spider_precision prec, int ry);
 
 // api.cu: enqueue `steps` steps in -> out on `stream` (plan lock held by the caller).
 spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
+// api.cu: upload the plan's operands (and allocate its scratch grid) if needed.
+spider_status ensure_plan_device(spider_plan_t* p, bool scratch);
 
 }  // namespace spider

@@ -261,15 +261,9 @@ __global__ void __launch_bounds__(C::kThreads)
       const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
       if (!__syncthreads_and(ok)) break;
     } else {
-      // Cooperative loads (grids whose rows are not 16-byte aligned).
-      for (int i = tid; i < C::kStageFloats; i += C::kThreads) {
-        const int xx = i % C::SX, yy = (i / C::SX) % C::SY, zz = i / (C::SX * C::SY);
-        const int64_t gx = (int64_t)x0 - kHaloX + xx, gy = (int64_t)y0 - C::RY + yy, gz = (int64_t)z0 - C::RZ + zz;
-        float v = 0.f;
-        if (gx >= 0 && gx < args.nx && gy >= 0 && gy < args.ny && gz >= 0 && gz < args.nz)
-          v = args.src[(gz * args.ny + gy) * args.nx + gx];
-        S[i] = v;
-      }
+      // Asynchronous copies (grids whose rows are not 16-byte aligned).
+      load_box_async(args.src, args.nx, args.ny, args.nz, (int64_t)x0 - kHaloX, (int64_t)y0 - C::RY,
+                     (int64_t)z0 - C::RZ, C::SX, C::SY, C::SZ, S, warp, C::kThreads / 32, lane);
       __syncthreads();
     }
 

@@ -161,11 +161,35 @@ def test_tf32_operands_decode_to_banded_kernel_rows(ndim, r):
     assert words.size == (2 * rz + 1) * na * 128 and meta.size == (2 * rz + 1) * na * 32
     words = words.reshape(-1, 32, 4)
     meta = meta.reshape(-1, 32)
+    # the TF32 weights the plan used: read back from the top half of each A
+    # (row m = 0: output x0, window position 4 + dx holds w[dz][a - ry][dx])
+    used = np.zeros_like(w3)
+    for dzi in range(2 * rz + 1):
+        for a in range(2 * ry + 1):
+            used[dzi, a] = decode_tf32(words[dzi * na + a], meta[dzi * na + a])[0, 4 - r:5 + r]
+    # every window matrix is the banded kernel of those weights
     for dzi in range(2 * rz + 1):
         for a in range(na):
             got = decode_tf32(words[dzi * na + a], meta[dzi * na + a])
-            want = tf32(expected_window(w3, a, ry, r, dzi))
-            assert np.array_equal(got, want), (dzi, a)
+            assert np.array_equal(got, expected_window(used, a, ry, r, dzi).astype(np.float32)), (dzi, a)
+    # each weight is one of its two TF32 neighbours, and the rounded weights
+    # sum at least as close to the FP32 sum as round-to-nearest does
+    bits = w3.view(np.uint32) & np.uint32(0xFFFFE000)
+    lo = bits.view(np.float32)
+    hi = (bits + np.uint32(0x2000)).view(np.float32)
+    assert np.all((used == lo) | (used == hi))
+    true_sum = w3.astype(np.float64).sum()
+    assert abs(used.astype(np.float64).sum() - true_sum) <= abs(tf32(w3).astype(np.float64).sum() - true_sum)
+    p.close()
+
+
+def test_tf32_sum_preserving_rounding_keeps_exact_weights():
+    w = np.zeros((3, 3), np.float32)
+    w[1, 1], w[0, 1], w[2, 1], w[1, 0], w[1, 2] = 0.5, 0.125, 0.125, 0.125, 0.125
+    p = spider.Plan(w, (16, 16), "star", "tf32")
+    words, meta = p.operands()
+    top = decode_tf32(words.reshape(-1, 32, 4)[1], meta.reshape(-1, 32)[1])
+    assert np.array_equal(top[0, 3:6], w[1])
     p.close()
 
 

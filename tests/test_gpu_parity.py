@@ -251,3 +251,117 @@ def test_autotune_keeps_results_within_tolerance():
     assert p2.autotune(a, b, 8) == (T, v)
     plan.close()
     p2.close()
+
+
+# ------------------------------------------------------------------ batch and serving
+
+def _batch_jobs():
+    jobs = []
+    g = np.random.default_rng(77)
+    shapes = [(300, 520), (64, 128), (1, 512), (257, 1000), (90, 132), (70, 130), (128, 256), (33, 64)]
+    for i, ext in enumerate(shapes):
+        r = 1 + i % 3
+        kind = "box" if i % 2 == 0 else "star"
+        u0 = g.uniform(0, 1, ext).astype(np.float32)
+        w = si.normalised_coeffs(2, r, kind, g)
+        steps = [1, 7, 12, 3, 20, 2, 9, 5][i]
+        jobs.append((u0, w, kind, steps))
+    return jobs
+
+
+def test_batch_persistent_queue_matches_individual_runs():
+    jobs = _batch_jobs()
+    plans, ins, outs, refs = [], [], [], []
+    for u0, w, kind, steps in jobs:
+        p = spider.Plan(w, u0.shape, kind, "tf32")
+        plans.append(p)
+        ins.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.full_like(ins[-1], float("nan")))
+        refs.append(gpu_run(u0, w, steps, kind, "tf32"))
+    spider.batch(plans, ins, outs, [j[3] for j in jobs])
+    torch.cuda.synchronize()
+    for k, (u0, w, kind, steps) in enumerate(jobs):
+        got = outs[k].cpu().numpy()
+        assert np.array_equal(got, refs[k]), k               # same tile arithmetic, bit for bit
+        assert np.array_equal(ins[k].cpu().numpy(), u0)
+    # and against the oracle for one job
+    u0, w, kind, steps = jobs[3]
+    check_close(outs[3].cpu().numpy(), oracle.stencil(u0, w, steps), ("sparse_tc", "tf32"))
+    for p in plans:
+        p.close()
+
+
+def test_batch_with_direct_jobs_and_precisions():
+    # jobs the queue does not take (3-D, split precision, rows not 16-byte
+    # aligned) run through their own plans in the same call
+    g = np.random.default_rng(5)
+    cases = [((20, 33, 72), 1, "box", "tf32"), ((100, 130), 2, "box", "tf32"), ((96, 256), 3, "box", "f16x2"),
+             ((128, 128), 1, "star", "tf32")]
+    plans, ins, outs, refs = [], [], [], []
+    for ext, r, kind, prec in cases:
+        u0 = g.uniform(0, 1, ext).astype(np.float32)
+        w = si.normalised_coeffs(len(ext), r, kind, g)
+        plans.append(spider.Plan(w, ext, kind, prec))
+        ins.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.empty_like(ins[-1]))
+        refs.append(gpu_run(u0, w, 6, kind, prec))
+    spider.batch(plans, ins, outs, [6] * len(cases))
+    torch.cuda.synchronize()
+    for k in range(len(cases)):
+        assert np.array_equal(outs[k].cpu().numpy(), refs[k]), k
+    for p in plans:
+        p.close()
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    import time
+    g = np.random.default_rng(9)
+    specs = [((256, 512), 3, "box", 40, 1e-3), ((64, 64, 64), 1, "star", 12, 1e-3), ((512, 512), 1, "star", 33, 1e-5),
+             ((300, 260), 2, "box", 25, 1e-3), ((48, 40, 36), 2, "box", 9, 1e-5), ((1024, 1024), 2, "star", 50, 1e-3)]
+    jobs = []
+    for ext, r, kind, steps, err in specs:
+        u0 = g.uniform(0, 1, ext).astype(np.float32)
+        w = si.normalised_coeffs(len(ext), r, kind, g)
+        jobs.append((u0, w, kind, steps, err))
+    server = spider.Server(8 << 30)
+    plans = [spider.Plan(w, u0.shape, kind, "tf32") for u0, w, kind, steps, err in jobs]
+    tickets = [server.submit(p, u0, steps, err) for p, (u0, w, kind, steps, err) in zip(plans, jobs)]
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        for t, (u0, *_rest) in zip(tickets, jobs):
+            if t in results:
+                continue
+            out = np.empty_like(u0)
+            done, lat = server.poll(t, out)
+            if done:
+                results[t] = (out, lat)
+        time.sleep(0.002)
+    assert len(results) == len(tickets)
+    for t, (u0, w, kind, steps, err) in zip(tickets, jobs):
+        out, lat = results[t]
+        assert lat > 0
+        prec = "f16x2" if err <= 1e-4 else "tf32"
+        alone = gpu_run(u0, w, steps, kind, prec)
+        ref = oracle.stencil(u0, w, steps)
+        rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+        assert rel <= (2e-5 if prec == "f16x2" else 3e-3)
+        # the server advances jobs in chunks; TF32 results are bit-identical to
+        # a lone run, split precisions agree to the last bits
+        if prec == "tf32":
+            assert np.array_equal(out, alone)
+        else:
+            assert np.linalg.norm(out - alone) <= 1e-6 * np.linalg.norm(alone)
+    server.close()
+    for p in plans:
+        p.close()
+
+
+def test_server_rejects_oversize_jobs():
+    server = spider.Server(1 << 20)
+    p = spider.Plan(np.ones((3, 3), np.float32) / 9, (1024, 1024), "box", "tf32")
+    with pytest.raises(spider.SpiderError) as ei:
+        server.submit(p, np.zeros((1024, 1024), np.float32), 3)
+    assert ei.value.status == 3          # SPIDER_ERR_OOM
+    server.close()
+    p.close()
