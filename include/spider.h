@@ -104,10 +104,11 @@ spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
  * build does not support for the plan's stencil return SPIDER_ERR_UNSUPPORTED. */
 spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);
 
-/* Tile shape of the fused kernels: 0 = warp units of 8 output rows,
- * 1 = 16 rows (more independent MMAs per warp, more registers), 2 = 8 rows
- * with registers capped so three CTAs share an SM.  Any other value returns
- * SPIDER_ERR_INVALID.  spider_plan_autotune sets it. */
+/* Tile shape of the fused kernels: 0 = warp units of 8 output rows and two
+ * input boxes in flight; 1 = 16 rows (more independent MMAs per warp), two
+ * boxes; 2 = 8 rows, one box, registers capped so three CTAs share an SM;
+ * 3 = 16 rows, one box.  Any other value returns SPIDER_ERR_INVALID.
+ * spider_plan_autotune sets it. */
 spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 
 /* spider_plan_autotune -- measures the plan's configurations on the caller's

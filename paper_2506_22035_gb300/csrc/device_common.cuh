@@ -16,6 +16,16 @@ constexpr int kStatusTimeout = 1;
 // A bounded wait gives up after this many SM clock cycles (~2 s at 2 GHz).
 constexpr long long kWaitCycles = 4000000000LL;
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while the previous kernel in the
+// stream finishes; it must wait here before touching any grid the previous
+// kernel reads or writes.  launch_dependents lets the next kernel's CTAs be
+// scheduled early (they wait in griddep_wait in turn).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -26,10 +26,11 @@
 
 namespace spider {
 
-template <int R_, int T_, int BY_, int BX_, int H_, int NW_, int MINB_ = 1>
+template <int R_, int T_, int BY_, int BX_, int H_, int NW_, int MINB_ = 1, int INS_ = 1>
 struct FuseCfg {
   static constexpr int RZ = 0, RY = R_, RX = R_, T = T_, BY = BY_, BX = BX_, H = H_, NW = NW_;
   static constexpr int kMinBlocks = MINB_;  // CTAs per SM the register budget must allow
+  static constexpr int kInStages = INS_;    // input boxes in flight: 1, or 2 (prefetch a whole tile ahead)
   static constexpr int NA = 2 * RY + 2;
   static constexpr int kThreads = NW * 32;
   // level t: 0 = input box, T = output tile
@@ -44,7 +45,7 @@ struct FuseCfg {
   static constexpr int kInStride = align1k(kInBytes);
   static constexpr int kPStride = T >= 2 ? align1k(rows(1) * pitch(1) * 4) : 0;  // odd levels
   static constexpr int kQStride = T >= 3 ? align1k(rows(2) * pitch(2) * 4) : 0;  // even levels
-  static constexpr int kSmemBytes = kInStride + kPStride + kQStride + 1024 + 64;
+  static constexpr int kSmemBytes = kInStages * kInStride + kPStride + kQStride + 1024 + 64;
   static_assert(T >= 2, "use the one-step kernel for T = 1");
   static_assert(BX % 8 == 0 && BX >= 64, "tile width");
   static_assert(width(0) <= 256 && rows(0) <= 256, "TMA box dimension limit");
@@ -215,27 +216,29 @@ template <class F, Mode MODE, int LV>
 struct LevelRunner {
   template <class... Ops>
   __device__ __forceinline__ static void run(const FusedCtx& c, float* in, float* P, float* Q, uint64_t* bar,
-                                             const CUtensorMap* tmap, int next_tile, Ops&... ops);
+                                             const CUtensorMap* tmap, int refill_tile, Ops&... ops);
 };
 
+// `in`/`bar`: the input box of this tile and its barrier; once level 1 has
+// read it, the box is refilled with `refill_tile` (if any).
 template <class F, Mode MODE, int LV>
 template <class... Ops>
 __device__ __forceinline__ void LevelRunner<F, MODE, LV>::run(const FusedCtx& c, float* in, float* P, float* Q,
-                                                              uint64_t* bar, const CUtensorMap* tmap, int next_tile,
+                                                              uint64_t* bar, const CUtensorMap* tmap, int refill_tile,
                                                               Ops&... ops) {
   const float* src = (LV == 1) ? in : ((LV - 1) % 2 == 1 ? P : Q);
   float* dst = (LV == F::T) ? nullptr : (LV % 2 == 1 ? P : Q);
   fused_level<F, MODE, LV>(c, src, dst, ops...);
   __syncthreads();
-  if (LV == 1 && threadIdx.x == 0 && next_tile >= 0) {
-    // the input box is no longer read: prefetch the next tile into it
+  if (LV == 1 && threadIdx.x == 0 && refill_tile >= 0) {
+    // the input box is no longer read: prefetch a later tile into it
     const StepArgs& args = *c.args;
-    const int tx = next_tile % args.tiles_x, ty = next_tile / args.tiles_x;
+    const int tx = refill_tile % args.tiles_x, ty = refill_tile / args.tiles_x;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, F::kInBytes);
     tma_load_3d(in, tmap, bar, tx * F::BX - 4 * F::T, ty * F::BY - F::RY * F::T, 0);
   }
-  if constexpr (LV < F::T) LevelRunner<F, MODE, LV + 1>::run(c, in, P, Q, bar, tmap, next_tile, ops...);
+  if constexpr (LV < F::T) LevelRunner<F, MODE, LV + 1>::run(c, in, P, Q, bar, tmap, refill_tile, ops...);
 }
 
 template <class F, Mode MODE>
@@ -244,10 +247,11 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
-  float* in = reinterpret_cast<float*>(smem);
-  float* P = reinterpret_cast<float*>(smem + F::kInStride);
-  float* Q = reinterpret_cast<float*>(smem + F::kInStride + F::kPStride);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + F::kInStride + F::kPStride + F::kQStride);
+  constexpr int NS = F::kInStages;
+  float* P = reinterpret_cast<float*>(smem + NS * F::kInStride);
+  float* Q = reinterpret_cast<float*>(smem + NS * F::kInStride + F::kPStride);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * F::kInStride + F::kPStride + F::kQStride);
+  auto in_box = [&](int s) { return reinterpret_cast<float*>(smem + s * F::kInStride); };
 
   FusedCtx c;
   c.args = &args;
@@ -259,14 +263,20 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
   const int ntiles = args.tiles_x * args.tiles_y;
 
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
     fence_mbar_init();
   }
+  griddep_wait();  // see stencil_step_kernel
+  griddep_launch_dependents();
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < ntiles) {
-    const int t = blockIdx.x, tx = t % args.tiles_x, ty = t / args.tiles_x;
-    mbar_arrive_expect_tx(bar, F::kInBytes);
-    tma_load_3d(in, &tmap, bar, tx * F::BX - 4 * F::T, ty * F::BY - F::RY * F::T, 0);
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      const int t = blockIdx.x + k * gridDim.x;
+      if (t >= ntiles) break;
+      const int tx = t % args.tiles_x, ty = t / args.tiles_x;
+      mbar_arrive_expect_tx(&bar[k], F::kInBytes);
+      tma_load_3d(in_box(k), &tmap, &bar[k], tx * F::BX - 4 * F::T, ty * F::BY - F::RY * F::T, 0);
+    }
   }
 
   constexpr int NA = F::NA;
@@ -308,16 +318,18 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
 
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    const bool ok = mbar_wait_bounded(bar, it & 1, args.status);
+    const int st = it % NS;
+    const uint32_t parity = (uint32_t)((it / NS) & 1);
+    const bool ok = mbar_wait_bounded(&bar[st], parity, args.status);
     if (!__syncthreads_and(ok)) {
       // the load we gave up on may still land: wait for it once more (bounded)
-      if (tid == 0) (void)mbar_wait_bounded(bar, it & 1, args.status);
+      if (tid == 0) (void)mbar_wait_bounded(&bar[st], parity, args.status);
       break;
     }
     c.x0 = (t % args.tiles_x) * F::BX;
     c.y0 = (t / args.tiles_x) * F::BY;
-    const int next = t + (int)gridDim.x < ntiles ? t + (int)gridDim.x : -1;
-    LevelRunner<F, MODE, 1>::run(c, in, P, Q, bar, &tmap, next, A, E, Ad, Am, Em, W);
+    const int refill = t + NS * (int)gridDim.x < ntiles ? t + NS * (int)gridDim.x : -1;
+    LevelRunner<F, MODE, 1>::run(c, in_box(st), P, Q, &bar[st], &tmap, refill, A, E, Ad, Am, Em, W);
   }
 }
 

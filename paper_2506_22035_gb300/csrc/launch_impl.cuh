@@ -11,6 +11,25 @@
 
 namespace spider {
 
+// Launch with programmatic stream serialization: the kernel may begin while
+// the previous kernel on the stream drains; the kernels wait (griddep_wait)
+// before touching the grids.
+template <class K>
+cudaError_t launch_pdl(K kern, int grid, int threads, int smem, cudaStream_t stream, const CUtensorMap& map,
+                       const StepArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, map, a);
+}
+
 template <class C, Mode MODE>
 cudaError_t launch_cfg(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
@@ -55,8 +74,7 @@ cudaError_t launch_cfg(const LaunchCtx& ctx) {
   const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
-  kern<<<grid, C::kThreads, C::kSmemBytes, ctx.stream>>>(map, a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
 
 // Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
@@ -124,34 +142,40 @@ cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
   const long long ntiles = (long long)a.tiles_x * a.tiles_y;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
-  kern<<<grid, F::kThreads, F::kSmemBytes, ctx.stream>>>(map, a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, F::kThreads, F::kSmemBytes, ctx.stream, map, a);
 }
 
 // Fused tile shapes: level 1 is 64 rows x 16 segments (two N-tiles), so the
 // output tile is BY = 64 - 2r(T-1) rows x BX = 8 (17 - T) columns; 8 warps;
-// warp units of H rows x 8 segments.  Variants: 0 -> H = 8; 1 -> H = 16;
-// 2 -> H = 8 with registers capped for 3 CTAs per SM.
-template <int R, int T, int H, int MINB>
-using FusedTile = FuseCfg<R, T, 64 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB>;
+// warp units of H rows x 8 segments.  Variants:
+//   0: H = 8,  two input boxes in flight      1: H = 16, two input boxes
+//   2: H = 8,  one input box, registers capped for 3 CTAs per SM
+//   3: H = 16, one input box
+template <int R, int T, int H, int MINB, int INS>
+using FusedTile = FuseCfg<R, T, 64 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB, INS>;
 
-template <Mode MODE, int R, int H, int MINB>
+template <Mode MODE, int R, int H, int MINB, int INS>
 cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
   switch (T) {
-    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB>, MODE>(ctx);
-    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB>, MODE>(ctx);
-    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB>, MODE>(ctx);
+    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB, INS>, MODE>(ctx);
+    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB, INS>, MODE>(ctx);
+    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB, INS>, MODE>(ctx);
     default: return cudaErrorNotSupported;
   }
 }
 
+// Variants 2 and 3 exist for the TF32 sparse mode only (the split and dense
+// modes need more registers than variant 2 allows); elsewhere they run as
+// variants 0 and 1.
 template <Mode MODE, int R>
 cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
-  switch (ctx.plan->tile_variant) {
-    case 1: return launch_fused_rh<MODE, R, 16, 1>(T, ctx);
-    case 2: return launch_fused_rh<MODE, R, 8, 3>(T, ctx);
-    default: return launch_fused_rh<MODE, R, 8, 1>(T, ctx);
+  int v = ctx.plan->tile_variant;
+  if (MODE != Mode::SpTF32 && v >= 2) v -= 2;
+  if constexpr (MODE == Mode::SpTF32) {
+    if (v == 2) return launch_fused_rh<MODE, R, 8, 3, 1>(T, ctx);
+    if (v == 3) return launch_fused_rh<MODE, R, 16, 1, 1>(T, ctx);
   }
+  return v == 1 ? launch_fused_rh<MODE, R, 16, 1, 2>(T, ctx) : launch_fused_rh<MODE, R, 8, 1, 2>(T, ctx);
 }
 
 template <Mode MODE>

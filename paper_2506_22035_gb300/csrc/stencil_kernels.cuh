@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(C::kThreads)
     mbar_init(&full[1], 1);
     fence_mbar_init();
   }
+  // the previous step's kernel may still be running: wait before reading the
+  // source grid or writing the destination (which it may be reading)
+  griddep_wait();
+  griddep_launch_dependents();
   __syncthreads();
   if (use_tma && tid == 0) {
     if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
