@@ -8,6 +8,7 @@
 #include "launch.h"
 #include "fused_kernels.cuh"
 #include "stencil_kernels.cuh"
+#include "stream3d_kernels.cuh"
 
 namespace spider {
 
@@ -77,13 +78,80 @@ cudaError_t launch_cfg(const LaunchCtx& ctx) {
   return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
 
+// 3-D z-streaming launch (TMA-describable grids); cudaErrorNotSupported
+// otherwise, and the caller uses the cube-tiled kernel.
+template <class C, Mode MODE>
+cudaError_t launch_stream3d(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, 1)) return cudaErrorNotSupported;
+  auto kern = stream3d_kernel<C, MODE>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
+  a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.use_tma = 1;
+  const long long ncol = (long long)a.tiles_x * a.tiles_y;
+  const long long slots = (long long)occ * ctx.sms;
+  // z chunks: enough items for four per resident CTA, chunks of >= 8 planes
+  long long nchunks = std::max<long long>(1, (4 * slots + ncol - 1) / ncol);
+  nchunks = std::min<long long>(nchunks, std::max<long long>(1, p->nz / 8));
+  if (ncol * nchunks > (1LL << 31) - 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ncol * nchunks, slots);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(C::kThreads);
+  cfg.dynamicSmemBytes = C::kSmemBytes;
+  cfg.stream = ctx.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, map, a, (int)nchunks);
+}
+
 // Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
-// 3-D (planes x 16 x 128 outputs).
+// 3-D (z-streaming 32 x 128 column blocks; cube tiles of planes x 16 x 128
+// outputs when the grid's rows are not TMA-describable).
 template <int R, Mode MODE>
 cudaError_t launch_class(int cls, const LaunchCtx& ctx) {
   if (cls == 1) return launch_cfg<TileCfg<0, 0, R, 1, 1, 2, 2>, MODE>(ctx);
   if (cls == 2) return launch_cfg<TileCfg<0, R, R, 1, 4, 2, 16>, MODE>(ctx);
-  if (cls == 3) return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE>(ctx);
+  if (cls == 3) {
+    const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE>(ctx);
+    if (e != cudaErrorNotSupported) return e;
+    return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE>(ctx);
+  }
   return cudaErrorNotSupported;
 }
 
