@@ -131,9 +131,16 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   // destination makes the last pass land in out.
   float* bufs[2] = {out, p->dev.scratch};
   const int first = (npasses % 2 == 1) ? 0 : 1;
+  // TF32 engines: every grid between two passes is stored rounded to TF32 as
+  // the next pass would round it, and that pass skips the rounding; the
+  // caller's input is rounded on load and the final grid is stored unrounded.
+  const bool tf32 = p->engine == SPIDER_ENGINE_DENSE_TC ||
+                    (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3);
   for (int64_t k = 0; k < npasses; ++k) {
     ctx.dst = bufs[(first + k) % 2];
     ctx.src = (k == 0) ? in : bufs[(first + k - 1) % 2];
+    ctx.in_tf32 = tf32 && k > 0;
+    ctx.out_tf32 = tf32 && k + 1 < npasses;
     cudaError_t e = launch_pass(ctx, k < full ? T : rem);
     if (e == cudaErrorNotSupported) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil/engine");
     if (e != cudaSuccess) return cuda_fail(e, "stencil pass launch");

@@ -63,7 +63,7 @@ struct FusedCtx {
 
 // One level LV: reads `src` (level LV-1), writes `dst` (level LV, shared
 // memory) or the output grid (LV == T).
-template <class F, Mode MODE, int LV>
+template <class F, Mode MODE, bool RIN, int LV>
 __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src, float* dst, const uint4 (&A)[F::NA],
                                             const uint32_t (&E)[F::NA], const uint4 (&Ad)[F::NA][2],
                                             const uint4 (&Am)[F::RY + 1], const uint32_t (&Em)[F::RY + 1],
@@ -136,9 +136,10 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
         for (int j = 0; j < 4; ++j) acc[i][j] = accC[i][j] = 0.f;
       const int ccol = 8 * (s0 + c.g) + 4 * ((c.q == 1) ? 2 : (c.q == 2) ? 1 : c.q);
       const float* row0 = src + r0 * SP + (LV >= 2 ? swz(ccol) : ccol);
-      // levels >= 2 read values this kernel stored already rounded to TF32
-      if (MODE == Mode::SpTF32) plane_sp_tf32<F, SP, LV == 1>(row0, A, E, acc);
-      else if (MODE == Mode::DenseTF32) plane_dense_tf32<F, SP, LV == 1>(row0, Ad, acc);
+      // levels >= 2 read values this kernel stored already rounded to TF32;
+      // level 1 reads the input grid, rounded already when RIN is false
+      if (MODE == Mode::SpTF32) plane_sp_tf32<F, SP, LV == 1 && RIN>(row0, A, E, acc);
+      else if (MODE == Mode::DenseTF32) plane_dense_tf32<F, SP, LV == 1 && RIN>(row0, Ad, acc);
       else if (MODE == Mode::SpF16x2) plane_sp_split<F, false, SP>(row0, Am, Em, A, E, acc, accC);
       else plane_sp_split<F, true, SP>(row0, Am, Em, A, E, acc, acc);
       if (MODE == Mode::SpF16x2) {
@@ -182,6 +183,7 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
             }
         }
       } else {
+        if (kStoreTF32 && args.out_tf32) round_tf32_inplace(acc);
         float* o = args.dst + (int64_t)gy0 * args.nx + gx0 + lx;
         const int nx = (int)args.nx;
         if (interior) {
@@ -212,7 +214,7 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
   }
 }
 
-template <class F, Mode MODE, int LV>
+template <class F, Mode MODE, bool RIN, int LV>
 struct LevelRunner {
   template <class... Ops>
   __device__ __forceinline__ static void run(const FusedCtx& c, float* in, float* P, float* Q, uint64_t* bar,
@@ -221,14 +223,14 @@ struct LevelRunner {
 
 // `in`/`bar`: the input box of this tile and its barrier; once level 1 has
 // read it, the box is refilled with `refill_tile` (if any).
-template <class F, Mode MODE, int LV>
+template <class F, Mode MODE, bool RIN, int LV>
 template <class... Ops>
-__device__ __forceinline__ void LevelRunner<F, MODE, LV>::run(const FusedCtx& c, float* in, float* P, float* Q,
+__device__ __forceinline__ void LevelRunner<F, MODE, RIN, LV>::run(const FusedCtx& c, float* in, float* P, float* Q,
                                                               uint64_t* bar, const CUtensorMap* tmap, int refill_tile,
                                                               Ops&... ops) {
   const float* src = (LV == 1) ? in : ((LV - 1) % 2 == 1 ? P : Q);
   float* dst = (LV == F::T) ? nullptr : (LV % 2 == 1 ? P : Q);
-  fused_level<F, MODE, LV>(c, src, dst, ops...);
+  fused_level<F, MODE, RIN, LV>(c, src, dst, ops...);
   __syncthreads();
   if (LV == 1 && threadIdx.x == 0 && refill_tile >= 0) {
     // the input box is no longer read: prefetch a later tile into it
@@ -238,10 +240,10 @@ __device__ __forceinline__ void LevelRunner<F, MODE, LV>::run(const FusedCtx& c,
     mbar_arrive_expect_tx(bar, F::kInBytes);
     tma_load_3d(in, tmap, bar, tx * F::BX - 4 * F::T, ty * F::BY - F::RY * F::T, 0);
   }
-  if constexpr (LV < F::T) LevelRunner<F, MODE, LV + 1>::run(c, in, P, Q, bar, tmap, refill_tile, ops...);
+  if constexpr (LV < F::T) LevelRunner<F, MODE, RIN, LV + 1>::run(c, in, P, Q, bar, tmap, refill_tile, ops...);
 }
 
-template <class F, Mode MODE>
+template <class F, Mode MODE, bool RIN = true>
 __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     fused_step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs args) {
   extern __shared__ unsigned char smem_raw[];
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     c.x0 = (t % args.tiles_x) * F::BX;
     c.y0 = (t / args.tiles_x) * F::BY;
     const int refill = t + NS * (int)gridDim.x < ntiles ? t + NS * (int)gridDim.x : -1;
-    LevelRunner<F, MODE, 1>::run(c, in_box(st), P, Q, &bar[st], &tmap, refill, A, E, Ad, Am, Em, W);
+    LevelRunner<F, MODE, RIN, 1>::run(c, in_box(st), P, Q, &bar[st], &tmap, refill, A, E, Ad, Am, Em, W);
   }
 }
 

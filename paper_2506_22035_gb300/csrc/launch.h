@@ -14,6 +14,11 @@ struct LaunchCtx {
   float* dst;
   cudaStream_t stream;
   int sms;
+  // TF32 modes only: the source grid holds values already rounded to TF32
+  // (written by the previous pass with out_tf32), and the destination grid
+  // is read by a later pass, so it may be stored rounded.
+  bool in_tf32 = false;
+  bool out_tf32 = false;
 };
 
 // Launches one time step src -> dst for the plan's engine and precision.

@@ -31,10 +31,10 @@ cudaError_t launch_pdl(K kern, int grid, int threads, int smem, cudaStream_t str
   return cudaLaunchKernelEx(&cfg, kern, map, a);
 }
 
-template <class C, Mode MODE>
-cudaError_t launch_cfg(const LaunchCtx& ctx) {
+template <class C, Mode MODE, bool RIN>
+cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
-  auto kern = stencil_step_kernel<C, MODE>;
+  auto kern = stencil_step_kernel<C, MODE, RIN>;
   // Per-device one-time setup: opt into the dynamic shared memory and read
   // the occupancy that sizes the persistent grid.
   static std::mutex mu;
@@ -72,21 +72,32 @@ cudaError_t launch_cfg(const LaunchCtx& ctx) {
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   a.use_tma = make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, C::SZ) ? 1 : 0;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
   return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
 
+// TF32 modes read a grid stored already rounded (ctx.in_tf32) with the
+// kernel that skips the operand rounding.
+template <class C, Mode MODE>
+cudaError_t launch_cfg(const LaunchCtx& ctx) {
+  if constexpr (is_tf32_mode(MODE)) {
+    if (ctx.in_tf32) return launch_cfg_k<C, MODE, false>(ctx);
+  }
+  return launch_cfg_k<C, MODE, true>(ctx);
+}
+
 // 3-D z-streaming launch (TMA-describable grids); cudaErrorNotSupported
 // otherwise, and the caller uses the cube-tiled kernel.
-template <class C, Mode MODE>
-cudaError_t launch_stream3d(const LaunchCtx& ctx) {
+template <class C, Mode MODE, bool RIN>
+cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, 1)) return cudaErrorNotSupported;
-  auto kern = stream3d_kernel<C, MODE>;
+  auto kern = stream3d_kernel<C, MODE, RIN>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
   int dev = 0;
@@ -120,6 +131,7 @@ cudaError_t launch_stream3d(const LaunchCtx& ctx) {
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
   a.use_tma = 1;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ncol = (long long)a.tiles_x * a.tiles_y;
   const long long slots = (long long)occ * ctx.sms;
   // z chunks: enough items for four per resident CTA, chunks of >= 8 planes
@@ -138,6 +150,14 @@ cudaError_t launch_stream3d(const LaunchCtx& ctx) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, map, a, (int)nchunks);
+}
+
+template <class C, Mode MODE>
+cudaError_t launch_stream3d(const LaunchCtx& ctx) {
+  if constexpr (is_tf32_mode(MODE)) {
+    if (ctx.in_tf32) return launch_stream3d_k<C, MODE, false>(ctx);
+  }
+  return launch_stream3d_k<C, MODE, true>(ctx);
 }
 
 // Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
@@ -166,14 +186,14 @@ cudaError_t launch_mode(int cls, int r, const LaunchCtx& ctx) {
 }
 
 // ---- temporal fusion (2-D) ----------------------------------------------
-template <class F, Mode MODE>
-cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
+template <class F, Mode MODE, bool RIN>
+cudaError_t launch_fused_cfg_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
   if (p->ndim != 2) return cudaErrorNotSupported;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, 1, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
-  auto kern = fused_step_kernel<F, MODE>;
+  auto kern = fused_step_kernel<F, MODE, RIN>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
   int dev = 0;
@@ -207,10 +227,19 @@ cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
   a.use_tma = 1;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ntiles = (long long)a.tiles_x * a.tiles_y;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
   return launch_pdl(kern, grid, F::kThreads, F::kSmemBytes, ctx.stream, map, a);
+}
+
+template <class F, Mode MODE>
+cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
+  if constexpr (is_tf32_mode(MODE)) {
+    if (ctx.in_tf32) return launch_fused_cfg_k<F, MODE, false>(ctx);
+  }
+  return launch_fused_cfg_k<F, MODE, true>(ctx);
 }
 
 // Fused tile shapes: level 1 is 64 rows x 16 segments (two N-tiles), so the

@@ -44,7 +44,25 @@ struct StepArgs {
   const float* w;          // coefficient cube (CUDA-core mode), float32
   int* status;             // device status word
   int use_tma;             // 1: TMA tile loads from `tmap`; 0: cooperative loads from src
+  int out_tf32;            // TF32 modes: store the outputs rounded to TF32 (the grid feeds another step)
 };
+
+// TF32 modes round every B operand to TF32 (round to nearest, ties away)
+// before the MMA.  A grid written for another step of the same run can hold
+// its values already rounded that way: the reading step then passes the raw
+// bits to the MMA (kernel template flag RIN = false) and gets bit-identical
+// results, at one rounding per stored point instead of one per operand
+// load (each input value is loaded about 2.75 times by overlapping windows
+// and warp tiles).
+__host__ __device__ constexpr bool is_tf32_mode(Mode m) { return m == Mode::SpTF32 || m == Mode::DenseTF32; }
+
+template <int N>
+__device__ __forceinline__ void round_tf32_inplace(float (&acc)[N][4]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = __uint_as_float(cvt_tf32(acc[i][j]));
+}
 
 template <int RZ_, int RY_, int RX_, int WZ_, int WY_, int WX_, int H_>
 struct TileCfg {
@@ -168,7 +186,7 @@ __device__ __forceinline__ void plane_sp_split(const float* row0, const uint4 (&
 }
 
 // --------------------------------------------------------------------------
-template <class C, Mode MODE>
+template <class C, Mode MODE, bool RIN = true>
 __global__ void __launch_bounds__(C::kThreads)
     stencil_step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs args) {
   extern __shared__ unsigned char smem_raw[];
@@ -331,8 +349,8 @@ __global__ void __launch_bounds__(C::kThreads)
         if (C::RZ != 0) load_operands(dzi);
         const float* row0 = S + (size_t)(wz + dzi) * C::SY * C::SX + (size_t)(wy * C::H) * C::SX + wx * 64 +
                             8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
-        if (MODE == Mode::SpTF32) plane_sp_tf32<C>(row0, A, E, acc);
-        else if (MODE == Mode::DenseTF32) plane_dense_tf32<C>(row0, Ad, acc);
+        if (MODE == Mode::SpTF32) plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
+        else if (MODE == Mode::DenseTF32) plane_dense_tf32<C, C::SX, RIN>(row0, Ad, acc);
         else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am, Em, A, E, acc, accC);
         else plane_sp_split<C, true>(row0, Am, Em, A, E, acc, acc);
       }
@@ -342,6 +360,7 @@ __global__ void __launch_bounds__(C::kThreads)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
       }
+      if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
       if (z < args.nz) {
         float* o = args.dst + (z * args.ny + ybase) * args.nx + xbase + 16 * q + g;
         const int nx = (int)args.nx;

@@ -31,7 +31,7 @@ struct StreamCfg {
   static_assert(SX <= 256 && SY <= 256, "TMA box dimension limit");
 };
 
-template <class C, Mode MODE>
+template <class C, Mode MODE, bool RIN = true>
 __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                const StepArgs args, int nchunks) {
   extern __shared__ unsigned char smem_raw[];
@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           if (!C::kAllOperands) load_operands(dzi, 0);
           const int k = C::kAllOperands ? dzi : 0;
           const float* row0 = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + coff;
-          if (MODE == Mode::SpTF32) plane_sp_tf32<C>(row0, A[k], E[k], acc);
-          else if (MODE == Mode::DenseTF32) plane_dense_tf32<C>(row0, Ad[k], acc);
+          if (MODE == Mode::SpTF32) plane_sp_tf32<C, C::SX, RIN>(row0, A[k], E[k], acc);
+          else if (MODE == Mode::DenseTF32) plane_dense_tf32<C, C::SX, RIN>(row0, Ad[k], acc);
           else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am[k], Em[k], A[k], E[k], acc, accC);
           else plane_sp_split<C, true>(row0, Am[k], Em[k], A[k], E[k], acc, acc);
         }
@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
         }
+        if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
         float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.nx + xbase + 16 * q + g;
         const int nx = (int)args.nx;
         if (ybase + C::H <= args.ny && xbase + 64 <= args.nx) {

@@ -223,6 +223,28 @@ def test_fused_passes_match_single_steps(key, r):
             assert np.linalg.norm(fused - single) <= 1e-6 * np.linalg.norm(single), (key, r, T)
 
 
+@pytest.mark.parametrize("engine", ["sparse_tc", "dense_tc"])
+@pytest.mark.parametrize("shape,r,T", [((1000,), 2, 1), ((300, 520), 3, 1), ((300, 520), 3, 2), ((300, 520), 1, 4),
+                                       ((301, 517), 2, 1), ((24, 40, 72), 1, 1), ((20, 33, 70), 2, 1)])
+def test_chained_calls_equal_one_multistep_call(engine, shape, r, T):
+    # One call of n steps stores the grids between its passes already rounded
+    # to TF32 and skips the operand rounding when it reads them; n calls of
+    # one step each round their input on load and store unrounded.  Both give
+    # every MMA the same operands: bit-identical results, for the one-step,
+    # fused, 3-D streaming and unaligned (non-TMA) kernels alike.
+    g = si.rng(12, r + 10 * len(shape))
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(len(shape), r, "box", g)
+    steps = 2 * T + 1  # full passes and a remainder pass
+    multi = gpu_run(u0, w, steps, "box", "tf32", engine, T)
+    u = u0
+    for _ in range(steps):
+        u = gpu_run(u, w, 1, "box", "tf32", engine, 1)
+    assert np.array_equal(multi, u), (engine, shape, r, T)
+    # the returned grid is not rounded to TF32 (FP32 accumulator values)
+    assert np.any(multi.view(np.uint32) & 0x1FFF)
+
+
 @pytest.mark.parametrize("T", [2, 3, 4])
 def test_fused_parity_with_oracle(T):
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
