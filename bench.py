@@ -105,13 +105,18 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
+# The files that define the stencil kernels, their geometry and their launch
+# configuration: a change to any of them invalidates recorded ncu counters.
+KERNEL_SOURCES = ("device_common.cuh", "fused_kernels.cuh", "launch.cu", "launch.h", "launch_impl.cuh",
+                  "spider_internal.h", "stencil_kernels.cuh", "stream3d_kernels.cuh")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_22035_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 

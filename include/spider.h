@@ -195,6 +195,52 @@ void spider_plan_destroy(spider_plan plan);
 spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                            const int64_t* steps, cudaStream_t stream);
 
+/* ---- domain decomposition: slabs with ghost planes ---------------------------
+ * The paper runs one GPU and has no counterpart; this is the hook a
+ * multi-GPU run builds on.  A domain cuts the grid of a plan into slabs along
+ * its slowest axis (z for 3-D, y for 2-D, x for 1-D).  Each slab owns a range
+ * of planes and keeps ghost planes, copies of its neighbours' outermost
+ * planes (the HALO region of Sec. 1 and Sec. 3.3.1 at the slab's edge).  A
+ * run alternates E time steps on every slab with an exchange of the ghost
+ * planes; the result equals spider_run's bit for bit.  All slabs live on the
+ * current device and the exchange is a device-to-device copy. */
+typedef struct spider_domain_t* spider_domain;
+
+/* spider_domain_create -- plans a run of `plan`'s grid as `parts` slabs.
+ *  plan               stencil, extents, precision, engine, steps per pass and
+ *                     tile variant of every slab (copied; the caller keeps it).
+ *  parts              >= 1 and <= the extent of the slowest axis.
+ *  steps_per_exchange E >= 1 time steps between exchanges; 0 selects the
+ *                     plan's steps per pass.
+ *  out                receives the domain (free with spider_domain_destroy).
+ * Interior sides get g ghost planes, E * radius rounded up to a multiple of 8
+ * (1-D) or 2 (2-D); slab boundaries are the even split rounded down to the
+ * same multiple, so every point keeps its place inside the tensor-core tiles.
+ * SPIDER_ERR_INVALID if a slab would own fewer than g planes (or none).
+ * Host work only; device memory (two grids per slab, plus each slab plan's
+ * scratch grid) is allocated on the first run. */
+spider_status spider_domain_create(spider_plan plan, int parts, int steps_per_exchange, spider_domain* out);
+
+/* Layout of slab i: first owned plane, owned planes, ghost planes below and
+ * above (0 at the grid's ends).  Any output pointer may be NULL. */
+spider_status spider_domain_slab(spider_domain domain, int i, int64_t* first, int64_t* owned, int64_t* ghost_lo,
+                                 int64_t* ghost_hi);
+
+/* spider_domain_run -- spider_run through the slabs: copies grid_in into the
+ * slabs (owned and ghost planes), runs ceil(steps / E) periods of E steps
+ * (the last may be shorter) with an exchange between periods, and copies the
+ * owned planes into grid_out.  grid_in, grid_out, steps, stream as for
+ * spider_run; asynchronous on `stream`.  Calls on one domain must not
+ * overlap on the GPU. */
+spider_status spider_domain_run(spider_domain domain, const float* grid_in, float* grid_out, int64_t steps,
+                                cudaStream_t stream);
+
+/* Blocks until the domain's work on `stream` is done and reports any
+ * device-side error, as spider_plan_sync. */
+spider_status spider_domain_sync(spider_domain domain, cudaStream_t stream);
+
+void spider_domain_destroy(spider_domain domain);
+
 /* GPU FP64 validation reductions (the only FP64 the library runs on the GPU).
  *   a    device float32 array of n values
  *   ref  device float64 array of n values, or NULL

@@ -153,6 +153,46 @@ def batch(plans, ins, outs, steps, stream=None) -> None:
     check(_native.load().spider_batch(n, P, I, O, S, _stream_handle(stream)), "spider_batch")
 
 
+class Domain:
+    """A plan's grid cut into slabs with ghost planes along its slowest axis
+    (spider_domain_create / run / sync); results equal Plan.run bit for bit."""
+
+    def __init__(self, plan: Plan, parts: int, steps_per_exchange: int = 0):
+        h = ctypes.c_void_p()
+        check(_native.load().spider_domain_create(plan.handle, int(parts), int(steps_per_exchange), ctypes.byref(h)),
+              "spider_domain_create")
+        self._h = h
+        self.parts = int(parts)
+        self.points = plan.points
+
+    def slab(self, i: int):
+        """(first owned plane, owned planes, ghost planes below, ghost planes above)."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        check(_native.load().spider_domain_slab(self._h, int(i), *[ctypes.byref(x) for x in v]), "spider_domain_slab")
+        return tuple(x.value for x in v)
+
+    def run(self, grid_in, grid_out, steps: int, stream=None) -> None:
+        for t in (grid_in, grid_out):
+            if not t.is_cuda or not t.is_contiguous() or t.numel() != self.points:
+                raise ValueError("grids must be contiguous CUDA tensors of the plan's size")
+        check(_native.load().spider_domain_run(self._h, _ptr(grid_in), _ptr(grid_out), int(steps),
+                                               _stream_handle(stream)), "spider_domain_run")
+
+    def sync(self, stream=None) -> None:
+        check(_native.load().spider_domain_sync(self._h, _stream_handle(stream)), "spider_domain_sync")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _native.load().spider_domain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching stencil server (spider_server_create / submit / poll)."""
 
@@ -191,5 +231,5 @@ class Server:
             pass
 
 
-__all__ = ["Plan", "Server", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
+__all__ = ["Plan", "Domain", "Server", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
            "PRECISIONS", "ENGINES", "SHAPES"]

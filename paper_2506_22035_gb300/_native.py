@@ -45,6 +45,12 @@ SIGNATURES = {
     "spider_plan_destroy": (None, [c_void_p]),
     "spider_batch": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                              ctypes.POINTER(c_int64), c_void_p]),
+    "spider_domain_create": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_void_p)]),
+    "spider_domain_slab": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                   ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+    "spider_domain_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "spider_domain_sync": (c_int, [c_void_p, c_void_p]),
+    "spider_domain_destroy": (None, [c_void_p]),
     "spider_norms_fp64": (c_int, [c_void_p, c_void_p, c_int64, ctypes.POINTER(c_double), c_void_p]),
     "spider_constant_check_fp64": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64), c_int64, c_double,
                                            ctypes.POINTER(c_double), c_void_p]),

@@ -240,3 +240,50 @@ def test_split_operands_have_expected_layout(prec):
                 nib = (int(m[c, lane]) >> (4 * k)) & 0xF
                 assert (nib & 3) < (nib >> 2)
     p.close()
+
+
+def _slabs(dom):
+    return [dom.slab(i) for i in range(dom.parts)]
+
+
+@pytest.mark.parametrize("extents,r,E,parts,align", [((300, 520), 3, 2, 3, 2), ((301, 64), 1, 3, 4, 2),
+                                                      ((1000,), 2, 1, 3, 8), ((20, 33, 70), 1, 3, 2, 1),
+                                                      ((64, 64), 2, 4, 1, 2)])
+def test_domain_layout(lib, extents, r, E, parts, align):
+    # host logic of the slab decomposition: owned ranges tile the slowest
+    # axis, ghost depth >= E * r rounded up to the tile alignment, boundaries
+    # on that alignment, and each ghost region lies inside the neighbour
+    nd = len(extents)
+    plan = spider.Plan(np.full((2 * r + 1,) * nd, 1.0 / (2 * r + 1) ** nd, np.float32), extents, "box")
+    plan.set_steps_per_pass(1)
+    dom = spider.Domain(plan, parts, E)
+    slabs = _slabs(dom)
+    g = 0 if parts == 1 else -(-E * r // align) * align
+    nxt = 0
+    for i, (first, owned, glo, ghi) in enumerate(slabs):
+        assert first == nxt and owned >= max(1, g)
+        assert first % align == 0
+        assert glo == (g if i > 0 else 0) and ghi == (g if i + 1 < parts else 0)
+        nxt = first + owned
+    assert nxt == extents[0]
+    dom.close()
+    plan.close()
+
+
+def test_domain_argument_validation(lib):
+    w = np.full((7, 7), 1 / 49, np.float32)
+    plan = spider.Plan(w, (10, 64), "box")
+    with pytest.raises(spider.SpiderError) as e:
+        spider.Domain(plan, 2, 4)            # ghost depth 12 > 5 owned planes
+    assert e.value.status == _native.SPIDER_ERR_INVALID
+    for parts, E in ((0, 1), (11, 1), (2, -1)):
+        with pytest.raises(spider.SpiderError):
+            spider.Domain(plan, parts, E)
+    h = ctypes.c_void_p()
+    assert lib.spider_domain_create(None, 2, 1, ctypes.byref(h)) == _native.SPIDER_ERR_INVALID
+    dom = spider.Domain(plan, 1, 4)          # one slab: no ghost planes needed
+    assert dom.slab(0) == (0, 10, 0, 0)
+    with pytest.raises(spider.SpiderError):
+        dom.slab(1)
+    dom.close()
+    plan.close()
