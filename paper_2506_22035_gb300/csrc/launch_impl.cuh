@@ -31,10 +31,10 @@ cudaError_t launch_pdl(K kern, int grid, int threads, int smem, cudaStream_t str
   return cudaLaunchKernelEx(&cfg, kern, map, a);
 }
 
-template <class C, Mode MODE, bool RIN>
+template <class C, Mode MODE, bool RIN, bool STAR>
 cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
-  auto kern = stencil_step_kernel<C, MODE, RIN>;
+  auto kern = stencil_step_kernel<C, MODE, RIN, STAR>;
   // Per-device one-time setup: opt into the dynamic shared memory and read
   // the occupancy that sizes the persistent grid.
   static std::mutex mu;
@@ -81,23 +81,23 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
 
 // TF32 modes read a grid stored already rounded (ctx.in_tf32) with the
 // kernel that skips the operand rounding.
-template <class C, Mode MODE>
+template <class C, Mode MODE, bool STAR = false>
 cudaError_t launch_cfg(const LaunchCtx& ctx) {
   if constexpr (is_tf32_mode(MODE)) {
-    if (ctx.in_tf32) return launch_cfg_k<C, MODE, false>(ctx);
+    if (ctx.in_tf32) return launch_cfg_k<C, MODE, false, STAR>(ctx);
   }
-  return launch_cfg_k<C, MODE, true>(ctx);
+  return launch_cfg_k<C, MODE, true, STAR>(ctx);
 }
 
 // 3-D z-streaming launch (TMA-describable grids); cudaErrorNotSupported
 // otherwise, and the caller uses the cube-tiled kernel.
-template <class C, Mode MODE, bool RIN>
+template <class C, Mode MODE, bool RIN, bool STAR>
 cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, 1)) return cudaErrorNotSupported;
-  auto kern = stream3d_kernel<C, MODE, RIN>;
+  auto kern = stream3d_kernel<C, MODE, RIN, STAR>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
   int dev = 0;
@@ -152,12 +152,12 @@ cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   return cudaLaunchKernelEx(&cfg, kern, map, a, (int)nchunks);
 }
 
-template <class C, Mode MODE>
+template <class C, Mode MODE, bool STAR = false>
 cudaError_t launch_stream3d(const LaunchCtx& ctx) {
   if constexpr (is_tf32_mode(MODE)) {
-    if (ctx.in_tf32) return launch_stream3d_k<C, MODE, false>(ctx);
+    if (ctx.in_tf32) return launch_stream3d_k<C, MODE, false, STAR>(ctx);
   }
-  return launch_stream3d_k<C, MODE, true>(ctx);
+  return launch_stream3d_k<C, MODE, true, STAR>(ctx);
 }
 
 // Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
@@ -168,6 +168,14 @@ cudaError_t launch_class(int cls, const LaunchCtx& ctx) {
   if (cls == 1) return launch_cfg<TileCfg<0, 0, R, 1, 1, 2, 2>, MODE>(ctx);
   if (cls == 2) return launch_cfg<TileCfg<0, R, R, 1, 4, 2, 16>, MODE>(ctx);
   if (cls == 3) {
+    // TF32 star stencils skip the zero operands of the off-centre planes
+    if constexpr (is_tf32_mode(MODE)) {
+      if (ctx.plan->shape == SPIDER_STAR) {
+        const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE, true>(ctx);
+        if (e != cudaErrorNotSupported) return e;
+        return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE, true>(ctx);
+      }
+    }
     const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE>(ctx);
     if (e != cudaErrorNotSupported) return e;
     return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE>(ctx);

@@ -87,7 +87,10 @@ struct TileCfg {
 
 // ROUND = false when the source already holds TF32 values (fused
 // intermediate levels), so the 13 low mantissa bits are already zero.
-template <class C, int SP, bool ROUND, int JJ>
+// Only the A indices AMIN..AMAX are applied (all of them by default); row
+// pair pp reads input rows 2pp + AMIN .. 2pp + AMAX, so the rows loaded are
+// AMIN .. H - 2 + AMAX.
+template <class C, int SP, bool ROUND, int JJ, int AMIN, int AMAX>
 __device__ __forceinline__ void sp_tf32_row(uint32_t addr, const uint4 (&A)[C::NA], const uint32_t (&E)[C::NA],
                                             float (&acc)[C::H / 2][4]) {
   const float4 v = lds128_at<JJ * SP * 4>(addr);
@@ -96,18 +99,18 @@ __device__ __forceinline__ void sp_tf32_row(uint32_t addr, const uint4 (&A)[C::N
 #pragma unroll
   for (int pp = 0; pp < C::H / 2; ++pp) {
     const int a = JJ - 2 * pp;
-    if (a >= 0 && a < C::NA) mma_sp_tf32(acc[pp], A[a], E[a], b);
+    if (a >= AMIN && a <= AMAX) mma_sp_tf32(acc[pp], A[a], E[a], b);
   }
-  if constexpr (JJ + 1 < C::H + 2 * C::RY) sp_tf32_row<C, SP, ROUND, JJ + 1>(addr, A, E, acc);
+  if constexpr (JJ + 1 <= C::H - 2 + AMAX) sp_tf32_row<C, SP, ROUND, JJ + 1, AMIN, AMAX>(addr, A, E, acc);
 }
 
-template <class C, int SP = C::SX, bool ROUND = true>
+template <class C, int SP = C::SX, bool ROUND = true, int AMIN = 0, int AMAX = C::NA - 1>
 __device__ __forceinline__ void plane_sp_tf32(const float* row0, const uint4 (&A)[C::NA],
                                               const uint32_t (&E)[C::NA], float (&acc)[C::H / 2][4]) {
-  sp_tf32_row<C, SP, ROUND, 0>(smem_u32(row0), A, E, acc);
+  sp_tf32_row<C, SP, ROUND, AMIN, AMIN, AMAX>(smem_u32(row0), A, E, acc);
 }
 
-template <class C, int SP, bool ROUND, int JJ>
+template <class C, int SP, bool ROUND, int JJ, int AMIN, int AMAX>
 __device__ __forceinline__ void dense_tf32_row(uint32_t addr, const uint4 (&A)[C::NA][2], float (&acc)[C::H / 2][4]) {
   const float4 v = lds128_at<JJ * SP * 4>(addr);
   const uint32_t b[4] = {ROUND ? cvt_tf32(v.x) : __float_as_uint(v.x), ROUND ? cvt_tf32(v.y) : __float_as_uint(v.y),
@@ -115,18 +118,34 @@ __device__ __forceinline__ void dense_tf32_row(uint32_t addr, const uint4 (&A)[C
 #pragma unroll
   for (int pp = 0; pp < C::H / 2; ++pp) {
     const int a = JJ - 2 * pp;
-    if (a >= 0 && a < C::NA) {
+    if (a >= AMIN && a <= AMAX) {
       mma_tf32(acc[pp], A[a][0], b[0], b[1]);
       mma_tf32(acc[pp], A[a][1], b[2], b[3]);
     }
   }
-  if constexpr (JJ + 1 < C::H + 2 * C::RY) dense_tf32_row<C, SP, ROUND, JJ + 1>(addr, A, acc);
+  if constexpr (JJ + 1 <= C::H - 2 + AMAX) dense_tf32_row<C, SP, ROUND, JJ + 1, AMIN, AMAX>(addr, A, acc);
 }
 
-template <class C, int SP = C::SX, bool ROUND = true>
+template <class C, int SP = C::SX, bool ROUND = true, int AMIN = 0, int AMAX = C::NA - 1>
 __device__ __forceinline__ void plane_dense_tf32(const float* row0, const uint4 (&A)[C::NA][2],
                                                  float (&acc)[C::H / 2][4]) {
-  dense_tf32_row<C, SP, ROUND, 0>(smem_u32(row0), A, acc);
+  dense_tf32_row<C, SP, ROUND, AMIN, AMIN, AMAX>(smem_u32(row0), A, acc);
+}
+
+// 3-D star stencils: a dz plane other than the centre holds only the
+// coefficient w[dz][0][0], i.e. kernel row dy = 0, which is A index ry for
+// the top output row and ry + 1 for the bottom one; the other A operands of
+// that plane are zero and are skipped (one MMA per input row instead of up
+// to ry + 1, and H input rows instead of H + 2ry).
+template <class C, int SP, bool ROUND>
+__device__ __forceinline__ void plane_sp_tf32_centre(const float* row0, const uint4 (&A)[C::NA],
+                                                     const uint32_t (&E)[C::NA], float (&acc)[C::H / 2][4]) {
+  plane_sp_tf32<C, SP, ROUND, C::RY, C::RY + 1>(row0, A, E, acc);
+}
+template <class C, int SP, bool ROUND>
+__device__ __forceinline__ void plane_dense_tf32_centre(const float* row0, const uint4 (&A)[C::NA][2],
+                                                        float (&acc)[C::H / 2][4]) {
+  plane_dense_tf32<C, SP, ROUND, C::RY, C::RY + 1>(row0, A, acc);
 }
 
 // Split precisions (FP16 hi/lo with the lo parts scaled by 2^11, or BF16
@@ -186,7 +205,7 @@ __device__ __forceinline__ void plane_sp_split(const float* row0, const uint4 (&
 }
 
 // --------------------------------------------------------------------------
-template <class C, Mode MODE, bool RIN = true>
+template <class C, Mode MODE, bool RIN = true, bool STAR = false>
 __global__ void __launch_bounds__(C::kThreads)
     stencil_step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs args) {
   extern __shared__ unsigned char smem_raw[];
@@ -245,12 +264,14 @@ __global__ void __launch_bounds__(C::kThreads)
     if (MODE == Mode::SpTF32) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
+        if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;  // zero operands
         A[a] = args.a_words[(size_t)(dzi * CPP + a) * 32 + lane];
         E[a] = args.meta[(size_t)(dzi * CPP + a) * 32 + lane];
       }
     } else if (MODE == Mode::DenseTF32) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
+        if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;
         Ad[a][0] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 0];
         Ad[a][1] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 1];
       }
@@ -349,10 +370,18 @@ __global__ void __launch_bounds__(C::kThreads)
         if (C::RZ != 0) load_operands(dzi);
         const float* row0 = S + (size_t)(wz + dzi) * C::SY * C::SX + (size_t)(wy * C::H) * C::SX + wx * 64 +
                             8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
-        if (MODE == Mode::SpTF32) plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
-        else if (MODE == Mode::DenseTF32) plane_dense_tf32<C, C::SX, RIN>(row0, Ad, acc);
-        else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am, Em, A, E, acc, accC);
-        else plane_sp_split<C, true>(row0, Am, Em, A, E, acc, acc);
+        const bool centre_only = STAR && dzi != C::RZ;
+        if (MODE == Mode::SpTF32) {
+          if (centre_only) plane_sp_tf32_centre<C, C::SX, RIN>(row0, A, E, acc);
+          else plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
+        } else if (MODE == Mode::DenseTF32) {
+          if (centre_only) plane_dense_tf32_centre<C, C::SX, RIN>(row0, Ad, acc);
+          else plane_dense_tf32<C, C::SX, RIN>(row0, Ad, acc);
+        } else if (MODE == Mode::SpF16x2) {
+          plane_sp_split<C, false>(row0, Am, Em, A, E, acc, accC);
+        } else {
+          plane_sp_split<C, true>(row0, Am, Em, A, E, acc, acc);
+        }
       }
       if (MODE == Mode::SpF16x2) {
 #pragma unroll

@@ -31,7 +31,7 @@ struct StreamCfg {
   static_assert(SX <= 256 && SY <= 256, "TMA box dimension limit");
 };
 
-template <class C, Mode MODE, bool RIN = true>
+template <class C, Mode MODE, bool RIN = true, bool STAR = false>
 __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                const StepArgs args, int nchunks) {
   extern __shared__ unsigned char smem_raw[];
@@ -70,12 +70,14 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
     if (MODE == Mode::SpTF32) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
+        if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;  // zero operands
         A[k][a] = args.a_words[(size_t)(dzi * CPP + a) * 32 + lane];
         E[k][a] = args.meta[(size_t)(dzi * CPP + a) * 32 + lane];
       }
     } else if (MODE == Mode::DenseTF32) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
+        if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;
         Ad[k][a][0] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 0];
         Ad[k][a][1] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 1];
       }
@@ -199,9 +201,14 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           if (!C::kAllOperands) load_operands(dzi, 0);
           const int k = C::kAllOperands ? dzi : 0;
           const float* row0 = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + coff;
-          if (MODE == Mode::SpTF32) plane_sp_tf32<C, C::SX, RIN>(row0, A[k], E[k], acc);
-          else if (MODE == Mode::DenseTF32) plane_dense_tf32<C, C::SX, RIN>(row0, Ad[k], acc);
-          else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am[k], Em[k], A[k], E[k], acc, accC);
+          const bool centre_only = STAR && dzi != C::RZ;  // see plane_sp_tf32_centre
+          if (MODE == Mode::SpTF32) {
+            if (centre_only) plane_sp_tf32_centre<C, C::SX, RIN>(row0, A[k], E[k], acc);
+            else plane_sp_tf32<C, C::SX, RIN>(row0, A[k], E[k], acc);
+          } else if (MODE == Mode::DenseTF32) {
+            if (centre_only) plane_dense_tf32_centre<C, C::SX, RIN>(row0, Ad[k], acc);
+            else plane_dense_tf32<C, C::SX, RIN>(row0, Ad[k], acc);
+          } else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am[k], Em[k], A[k], E[k], acc, accC);
           else plane_sp_split<C, true>(row0, Am[k], Em[k], A[k], E[k], acc, acc);
         }
         if (MODE == Mode::SpF16x2) {

@@ -245,6 +245,22 @@ def test_chained_calls_equal_one_multistep_call(engine, shape, r, T):
     assert np.any(multi.view(np.uint32) & 0x1FFF)
 
 
+@pytest.mark.parametrize("engine", ["sparse_tc", "dense_tc"])
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(18, 40, 72), (13, 35, 70)])
+def test_star_3d_skips_zero_operands(engine, r, shape):
+    # A 3-D star plan skips the A operands of its off-centre planes that hold
+    # only zero coefficients; a box plan with the same coefficients still
+    # issues them.  Adding exact zeros changes nothing: equal results.
+    g = si.rng(14, r)
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(3, r, "star", g)
+    star = gpu_run(u0, w, 3, "star", "tf32", engine)
+    box = gpu_run(u0, w, 3, "box", "tf32", engine)
+    assert np.array_equal(star, box), (engine, r, shape)
+    check_close(star, oracle.stencil(u0, w, 3), (engine, "tf32"))
+
+
 @pytest.mark.parametrize("T", [2, 3, 4])
 def test_fused_parity_with_oracle(T):
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
