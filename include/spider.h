@@ -100,20 +100,26 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
  * precision ignored). */
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
-/* Time steps fused per pass over HBM (1 = one launch per step).  Values the
- * build does not support for the plan's stencil return SPIDER_ERR_UNSUPPORTED. */
+/* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4
+ * for 2-D stencils and for 3-D radius-1 plans with the sparse engine in TF32;
+ * 1 otherwise.  Values the build does not support for the plan's stencil
+ * return SPIDER_ERR_UNSUPPORTED.  Grids whose rows TMA cannot describe run
+ * one step per pass whatever the setting. */
 spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);
 
-/* Tile shape of the fused kernels: 0 = warp units of 8 output rows and two
- * input boxes in flight; 1 = 16 rows (more independent MMAs per warp), two
+/* Tile shape of the fused kernels.  2-D: 0 = warp units of 8 output rows and
+ * two input boxes in flight; 1 = 16 rows (more independent MMAs per warp), two
  * boxes; 2 = 8 rows, one box, registers capped so three CTAs share an SM;
- * 3 = 16 rows, one box.  Any other value returns SPIDER_ERR_INVALID.
- * spider_plan_autotune sets it. */
+ * 3 = 16 rows, one box.  3-D: 0 = column blocks of 16 level-1 rows, warp
+ * units of 4 rows; 1 and 3 = 32 rows, units of 8; 2 = as 0 with registers
+ * capped for three CTAs per SM at 2 steps per pass.  Any other value returns
+ * SPIDER_ERR_INVALID.  spider_plan_autotune sets it. */
 spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 
 /* spider_plan_autotune -- measures the plan's configurations on the caller's
- * grids and keeps the fastest: time steps per pass 1..4 (2-D stencils) and
- * the tile variant.  Each candidate runs `steps` steps from grid_in into
+ * grids and keeps the fastest: time steps per pass 1..4 (where built, see
+ * spider_plan_set_steps_per_pass) and the tile variant.  Each candidate runs
+ * `steps` steps from grid_in into
  * grid_out (device grids as for spider_run; grid_out is overwritten) once to
  * warm up and twice timed with CUDA events on `stream`; the call is
  * synchronous.  Results are cached per (ndim, radius, shape, precision,

@@ -6,6 +6,8 @@
 #include <string>
 
 #include "launch.h"
+#include <algorithm>
+
 #include "spider_internal.h"
 
 namespace spider {
@@ -103,6 +105,13 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 }
 
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
+int max_steps_per_pass(const spider_plan_t* p) {
+  if (p->ndim == 2) return 4;
+  const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
+  if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
+  return 1;
+}
+
 spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
   const size_t bytes = (size_t)p->points() * sizeof(float);
   if (steps == 0) {
@@ -121,9 +130,9 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   ctx.sms = device_sm_count();
   // Passes of T fused time steps (2-D grids whose rows and buffers are
   // 16-byte aligned, as TMA requires), then one pass with the remainder.
-  int T = p->steps_per_pass;
+  int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
   auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  if (T > 1 && !(p->ndim == 2 && p->nx % 4 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch))) T = 1;
+  if (T > 1 && !(p->nx % 4 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch))) T = 1;
   const int64_t full = steps / T;
   const int rem = (int)(steps % T);
   const int64_t npasses = full + (rem ? 1 : 0);
@@ -235,8 +244,9 @@ spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
 spider_status spider_plan_set_steps_per_pass(spider_plan p, int steps_per_pass) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
   if (steps_per_pass < 1) return fail(SPIDER_ERR_INVALID, "steps_per_pass must be >= 1");
-  if (steps_per_pass > 1 && (p->ndim != 2 || steps_per_pass > 4))
-    return fail(SPIDER_ERR_UNSUPPORTED, "temporal fusion is built for 2-D stencils, 2..4 steps per pass");
+  if (steps_per_pass > max_steps_per_pass(p))
+    return fail(SPIDER_ERR_UNSUPPORTED,
+                "temporal fusion is built for 2-D stencils and for 3-D radius-1 sparse TF32 plans, 2..4 steps per pass");
   p->steps_per_pass = steps_per_pass;
   return SPIDER_OK;
 }

@@ -57,7 +57,7 @@ extern "C" spider_status spider_plan_autotune(spider_plan p, const float* grid_i
   }
   std::lock_guard<std::mutex> plock(p->mu);
   const int old_T = p->steps_per_pass, old_v = p->tile_variant;
-  const int maxT = p->ndim == 2 ? 4 : 1;
+  const int maxT = max_steps_per_pass(p);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(SPIDER_ERR_CUDA, "cudaEventCreate");

@@ -208,7 +208,7 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
   spider_status st = spider_plan_create(plan->ndim, plan->extents, plan->shape, plan->r, plan->w.data(), prec, &copy);
   if (st != SPIDER_OK) return st;
   if (plan->engine != SPIDER_ENGINE_SPARSE_TC) spider_plan_set_engine(copy, plan->engine);
-  copy->steps_per_pass = (plan->ndim == 2) ? plan->steps_per_pass : 1;
+  copy->steps_per_pass = std::min(plan->steps_per_pass, max_steps_per_pass(copy));
   copy->tile_variant = plan->tile_variant;
   auto j = std::make_unique<Job>();
   j->plan = copy;

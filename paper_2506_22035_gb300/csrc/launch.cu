@@ -75,6 +75,11 @@ namespace spider {
 cudaError_t launch_pass(const LaunchCtx& ctx, int T) {
   if (T <= 1) return launch_step(ctx);
   const spider_plan_t* p = ctx.plan;
+  if (p->ndim == 3) {
+    if (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3)
+      return launch_fused3d_sp_tf32(p->r, T, ctx);
+    return cudaErrorNotSupported;
+  }
   switch (p->engine) {
     case SPIDER_ENGINE_CUDA_CORE: return launch_fused_cuda_core(p->r, T, ctx);
     case SPIDER_ENGINE_DENSE_TC: return launch_fused_dense_tf32(p->r, T, ctx);

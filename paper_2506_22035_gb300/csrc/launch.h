@@ -43,6 +43,9 @@ cudaError_t launch_fused_sp_f16x2(int r, int T, const LaunchCtx& ctx);
 cudaError_t launch_fused_sp_bf16x3(int r, int T, const LaunchCtx& ctx);
 cudaError_t launch_fused_dense_tf32(int r, int T, const LaunchCtx& ctx);
 cudaError_t launch_fused_cuda_core(int r, int T, const LaunchCtx& ctx);
+// Fused passes of T = 2..4 time steps for 3-D stencils of radius 1 (TF32
+// modes, TMA-describable grids).
+cudaError_t launch_fused3d_sp_tf32(int r, int T, const LaunchCtx& ctx);
 
 // Builds a 3-D tiled tensor map over a float32 grid (nz, ny, nx) with the
 // given box; out-of-range box elements read as zero.  Returns false if the

@@ -8,6 +8,7 @@
 #include "launch.h"
 #include "fused_kernels.cuh"
 #include "stencil_kernels.cuh"
+#include "stream3d_fused_kernels.cuh"
 #include "stream3d_kernels.cuh"
 
 namespace spider {
@@ -289,6 +290,105 @@ cudaError_t launch_fused_mode(int r, int T, const LaunchCtx& ctx) {
     case 1: return launch_fused_r<MODE, 1>(T, ctx);
     case 2: return launch_fused_r<MODE, 2>(T, ctx);
     case 3: return launch_fused_r<MODE, 3>(T, ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+
+// ---- temporal fusion (3-D, z-streaming) -----------------------------------
+template <class F, Mode MODE, bool RIN, bool STAR>
+cudaError_t launch_fused3d_k(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  if (p->ndim != 3) return cudaErrorNotSupported;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
+  auto kern = stream3d_fused_kernel<F, MODE, RIN, STAR>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, F::kThreads, F::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.tiles_x = (int)((p->nx + F::BX - 1) / F::BX);
+  a.tiles_y = (int)((p->ny + F::BY - 1) / F::BY);
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.use_tma = 1;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
+  const long long ncol = (long long)a.tiles_x * a.tiles_y;
+  const long long slots = (long long)occ * ctx.sms;
+  // z chunks: about four items per resident CTA, chunks of >= 32 planes (each
+  // chunk recomputes 2r(T-t) planes of level t at its ends)
+  long long nchunks = std::max<long long>(1, (4 * slots + ncol - 1) / ncol);
+  nchunks = std::min<long long>(nchunks, std::max<long long>(1, p->nz / 32));
+  if (ncol * nchunks > (1LL << 31) - 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ncol * nchunks, slots);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(F::kThreads);
+  cfg.dynamicSmemBytes = F::kSmemBytes;
+  cfg.stream = ctx.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, map, a, (int)nchunks);
+}
+
+template <class F, Mode MODE>
+cudaError_t launch_fused3d_cfg(const LaunchCtx& ctx) {
+  const bool star = ctx.plan->shape == SPIDER_STAR;
+  if (ctx.in_tf32) {
+    return star ? launch_fused3d_k<F, MODE, false, true>(ctx) : launch_fused3d_k<F, MODE, false, false>(ctx);
+  }
+  return star ? launch_fused3d_k<F, MODE, true, true>(ctx) : launch_fused3d_k<F, MODE, true, false>(ctx);
+}
+
+// 3-D fused column blocks (r = 1): level 1 is L1Y rows x 128 columns.
+//   variant 0: L1Y = 16, warp units of 4 rows, 8 warps, registers for 2 CTAs
+//              per SM (1 for T = 4, whose rings need 114 KB)
+//   variant 1, 3: L1Y = 32, warp units of 8 rows, 8 warps, one CTA per SM
+//   variant 2: as 0 with registers capped for 3 CTAs per SM at T = 2
+template <Mode MODE, int T>
+cudaError_t launch_fused3d_t(const LaunchCtx& ctx) {
+  constexpr int kMinB = T == 4 ? 1 : 2;
+  const int v = ctx.plan->tile_variant;
+  if (v % 2 == 1) return launch_fused3d_cfg<Fuse3Cfg<1, T, 32, 8, 8, 1>, MODE>(ctx);
+  if (T == 2 && v == 2) return launch_fused3d_cfg<Fuse3Cfg<1, T, 16, 4, 8, 3>, MODE>(ctx);
+  return launch_fused3d_cfg<Fuse3Cfg<1, T, 16, 4, 8, kMinB>, MODE>(ctx);
+}
+
+template <Mode MODE>
+cudaError_t launch_fused3d_mode(int r, int T, const LaunchCtx& ctx) {
+  if (r != 1) return cudaErrorNotSupported;
+  switch (T) {
+    case 2: return launch_fused3d_t<MODE, 2>(ctx);
+    case 3: return launch_fused3d_t<MODE, 3>(ctx);
+    case 4: return launch_fused3d_t<MODE, 4>(ctx);
     default: return cudaErrorNotSupported;
   }
 }

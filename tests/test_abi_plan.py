@@ -86,7 +86,7 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     assert lib.spider_plan_set_tile_variant(p.handle, 1) == _native.SPIDER_OK
     assert lib.spider_plan_autotune(p.handle, None, None, 1, None, None, None) == _native.SPIDER_ERR_INVALID
     p.close()
-    p3 = spider.Plan(np.ones((3, 3, 3), np.float32), (8, 8, 8))
+    p3 = spider.Plan(np.ones((5, 5, 5), np.float32), (8, 8, 8))  # 3-D fusion is built for r = 1 only
     assert lib.spider_plan_set_steps_per_pass(p3.handle, 2) == _native.SPIDER_ERR_UNSUPPORTED
     p3.close()
 
@@ -287,3 +287,27 @@ def test_domain_argument_validation(lib):
         dom.slab(1)
     dom.close()
     plan.close()
+
+
+def test_steps_per_pass_where_fusion_is_built(lib):
+    # fused passes exist for 2-D stencils and for 3-D radius-1 sparse TF32 plans
+    def plan(nd, r, prec="tf32"):
+        return spider.Plan(np.full((2 * r + 1,) * nd, 0.1, np.float32), (16,) * nd, "box", prec)
+    for nd, r, prec, ok in ((2, 3, "tf32", True), (2, 1, "f16x2", True), (3, 1, "tf32", True),
+                            (3, 2, "tf32", False), (3, 1, "f16x2", False), (1, 1, "tf32", False)):
+        p = plan(nd, r, prec)
+        for T in (2, 4):
+            if ok:
+                p.set_steps_per_pass(T)
+            else:
+                with pytest.raises(spider.SpiderError) as e:
+                    p.set_steps_per_pass(T)
+                assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
+        with pytest.raises(spider.SpiderError):
+            p.set_steps_per_pass(5)
+        p.close()
+    p = plan(3, 1)
+    p.set_engine("dense_tc")
+    with pytest.raises(spider.SpiderError):
+        p.set_steps_per_pass(2)
+    p.close()

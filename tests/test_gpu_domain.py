@@ -47,6 +47,7 @@ def _run_both(u0, w, steps, shape, prec, engine, T, parts, E):
     ((200, 264), 1, "tf32", "cuda_core", 1, 3, 2, 5),
     ((4000,), 2, "tf32", "sparse_tc", 1, 3, 3, 8),          # 1-D, x slabs on 8-point segments
     ((24, 40, 72), 1, "tf32", "sparse_tc", 1, 2, 2, 5),     # 3-D z slabs, z-streaming kernel
+    ((40, 24, 72), 1, "tf32", "sparse_tc", 2, 2, 2, 7),     # 3-D fused passes
     ((20, 33, 70), 2, "f16x2", "sparse_tc", 1, 2, 1, 3),    # 3-D, unaligned rows
 ])
 def test_domain_run_equals_undivided_run(shape, r, prec, engine, T, parts, E, steps):

@@ -261,6 +261,23 @@ def test_star_3d_skips_zero_operands(engine, r, shape):
     check_close(star, oracle.stencil(u0, w, 3), (engine, "tf32"))
 
 
+@pytest.mark.parametrize("shape_kind", ["star", "box"])
+@pytest.mark.parametrize("shape", [(70, 40, 72), (9, 37, 136), (2, 20, 260), (1, 16, 64)])
+def test_fused_3d_passes_match_single_steps(shape_kind, shape):
+    # 3-D passes of T steps stream z planes through per-level rings; every
+    # level plane outside the grid is zero, so they repeat the products and
+    # roundings of T single steps: bit-identical.  (70, 40, 72) runs two z
+    # chunks; nz = 1, 2 leave most level planes outside the grid.
+    g = si.rng(15, shape[0])
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(3, 1, shape_kind, g)
+    single = gpu_run(u0, w, 7, shape_kind, "tf32", "sparse_tc", 1)
+    for T, variant in ((2, 0), (3, 1), (4, 2), (2, 2), (4, 1), (3, 0), (2, 3), (4, 0), (2, 1), (3, 2)):
+        fused = gpu_run(u0, w, 7, shape_kind, "tf32", "sparse_tc", T, variant)
+        assert np.array_equal(fused, single), (shape, T, variant)
+    check_close(single, oracle.stencil(u0, w, 7), ("sparse_tc", "tf32"))
+
+
 @pytest.mark.parametrize("T", [2, 3, 4])
 def test_fused_parity_with_oracle(T):
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
