@@ -108,7 +108,7 @@ def measured_peaks():
 # The files that define the stencil kernels, their geometry and their launch
 # configuration: a change to any of them invalidates recorded ncu counters.
 KERNEL_SOURCES = ("device_common.cuh", "fused_kernels.cuh", "launch.cu", "launch.h", "launch_impl.cuh",
-                  "spider_internal.h", "stencil_kernels.cuh", "stream3d_kernels.cuh")
+                  "spider_internal.h", "stencil_kernels.cuh", "stream3d_fused_kernels.cuh", "stream3d_kernels.cuh")
 
 
 def kernel_source_sha() -> str:
@@ -355,8 +355,10 @@ def run_spider(a):
         peaks, peak_kind = measured_peaks()
         alg_bytes = 8.0 * pts  # read every point once and write it once per pass
         achieved = alg_bytes / per_launch_s / 1e9
-        kernel = ("fused_step_kernel" if T > 1 else
-                  "stream3d_kernel" if wl.ndim == 3 else "stencil_step_kernel")
+        if wl.ndim == 3:
+            kernel = "stream3d_fused_kernel" if T > 1 else "stream3d_kernel"
+        else:
+            kernel = "fused_step_kernel" if T > 1 else "stencil_step_kernel"
         # every tile variant of a given T loads the same boxes and writes the
         # same tiles, so DRAM traffic is keyed by T only
         kernel_key = f"{kernel} {wl.name} {a.engine} {a.precision} T{T}"
