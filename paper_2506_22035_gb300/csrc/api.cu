@@ -33,12 +33,20 @@ static spider_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
   } while (0)
 
+static void drop_graphs(spider_plan_t* p) {
+  for (auto& g : p->dev.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  p->dev.graphs.clear();
+}
+
 static void free_device(spider_plan_t* p) {
   DeviceState& d = p->dev;
   if (d.device >= 0) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != d.device) cudaSetDevice(d.device);
+    drop_graphs(p);
+    if (d.capture_stream) cudaStreamDestroy(d.capture_stream);
     cudaFree(d.a_words);
     cudaFree(d.meta_words);
     cudaFree(d.w_dense);
@@ -157,6 +165,80 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   return SPIDER_OK;
 }
 
+// Repeated runs replay a CUDA graph.  A time-stepping loop calls spider_run
+// with the same grids and step count again and again; for small grids the
+// host cost of its launches (tensor-map encoding, one launch per pass) is
+// larger than the kernels.  The first call with a given (grids, steps,
+// configuration) runs directly and is remembered; the second captures the
+// same launches on a private stream (thread-local capture mode, after every
+// allocation the run needs) and instantiates them; later calls launch that
+// graph on the caller's stream.  Graphs hold the grids' addresses, which is
+// all a run depends on besides the plan's own buffers, and are dropped when
+// the plan's device state is.
+constexpr size_t kMaxRunGraphs = 8;
+
+static spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (steps < 1 || cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return run_device(p, in, out, steps, stream);  // the caller is capturing: plain launches
+  }
+  DeviceState& d = p->dev;
+  RunGraph* hit = nullptr;
+  for (auto& g : d.graphs)
+    if (g.in == in && g.out == out && g.steps == steps && g.steps_per_pass == p->steps_per_pass &&
+        g.tile_variant == p->tile_variant && g.engine == (int)p->engine)
+      hit = &g;
+  if (hit && hit->exec) {
+    hit->last_use = ++d.graph_clock;
+    SPIDER_CUDA(cudaGraphLaunch(hit->exec, stream));
+    return SPIDER_OK;
+  }
+  if (!hit) {
+    if (d.graphs.size() >= kMaxRunGraphs) {
+      auto lru = d.graphs.begin();
+      for (auto it = d.graphs.begin(); it != d.graphs.end(); ++it)
+        if (it->last_use < lru->last_use) lru = it;
+      if (lru->exec) cudaGraphExecDestroy(lru->exec);
+      d.graphs.erase(lru);
+    }
+    RunGraph g;
+    g.in = in;
+    g.out = out;
+    g.steps = steps;
+    g.steps_per_pass = p->steps_per_pass;
+    g.tile_variant = p->tile_variant;
+    g.engine = (int)p->engine;
+    g.last_use = ++d.graph_clock;
+    d.graphs.push_back(g);
+    return run_device(p, in, out, steps, stream);  // first sight: run directly
+  }
+  // second sight: capture
+  hit->last_use = ++d.graph_clock;
+  spider_status s = ensure_device(p);
+  if (s == SPIDER_OK && steps > 1) s = ensure_scratch(p);
+  if (s != SPIDER_OK) return s;
+  if (!d.capture_stream) SPIDER_CUDA(cudaStreamCreateWithFlags(&d.capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaStreamBeginCapture(d.capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const spider_status rs = run_device(p, in, out, steps, d.capture_stream);
+    ok = cudaStreamEndCapture(d.capture_stream, &graph) == cudaSuccess && rs == SPIDER_OK && graph;
+  }
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    // capture is an optimisation only: run the launches directly
+    cudaGetLastError();
+    set_error("");
+    return run_device(p, in, out, steps, stream);
+  }
+  hit->exec = exec;
+  SPIDER_CUDA(cudaGraphLaunch(exec, stream));
+  return SPIDER_OK;
+}
+
 }  // namespace spider
 
 using namespace spider;
@@ -231,8 +313,10 @@ spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
   p->engine = engine;
   spider_status s = build_operands(p);
   if (s != SPIDER_OK) return s;
-  // drop device copies of the old operands; they are uploaded again lazily
+  // drop device copies of the old operands (uploaded again lazily) and the
+  // run graphs that read them
   if (p->dev.device >= 0) {
+    drop_graphs(p);
     cudaFree(p->dev.a_words);
     cudaFree(p->dev.meta_words);
     p->dev.a_words = nullptr;
@@ -276,7 +360,7 @@ spider_status spider_run(spider_plan p, const float* grid_in, float* grid_out, i
   if (overlaps(grid_in, grid_out, (size_t)p->points() * sizeof(float)))
     return fail(SPIDER_ERR_INVALID, "grid_out overlaps grid_in");
   std::lock_guard<std::mutex> lock(p->mu);
-  return run_device(p, grid_in, grid_out, steps, stream);
+  return run_cached(p, grid_in, grid_out, steps, stream);
 }
 
 spider_status spider_run_host(spider_plan p, const float* host_in, float* host_out, int64_t steps,
@@ -298,7 +382,7 @@ spider_status spider_run_host(spider_plan p, const float* host_in, float* host_o
     }
   }
   SPIDER_CUDA(cudaMemcpyAsync(p->dev.host_stage_in, host_in, bytes, cudaMemcpyHostToDevice, stream));
-  s = run_device(p, p->dev.host_stage_in, p->dev.host_stage_out, steps, stream);
+  s = run_cached(p, p->dev.host_stage_in, p->dev.host_stage_out, steps, stream);
   if (s != SPIDER_OK) return s;
   SPIDER_CUDA(cudaMemcpyAsync(host_out, p->dev.host_stage_out, bytes, cudaMemcpyDeviceToHost, stream));
   SPIDER_CUDA(cudaStreamSynchronize(stream));

@@ -46,8 +46,21 @@ inline int phi_16bit(int kk) {  // kk in [0, 16) within one K half
 }
 
 // -------------------------------------------------------------- the plan
+// A captured whole run of spider_run (see run_cached in api.cu).
+struct RunGraph {
+  const float* in = nullptr;
+  float* out = nullptr;
+  int64_t steps = 0;
+  int steps_per_pass = 0, tile_variant = 0, engine = 0;
+  cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
+  uint64_t last_use = 0;
+};
+
 struct DeviceState {
   int device = -1;
+  std::vector<RunGraph> graphs;    // at most kMaxRunGraphs, least recently used evicted
+  cudaStream_t capture_stream = nullptr;
+  uint64_t graph_clock = 0;
   uint32_t* a_words = nullptr;     // packed A fragments
   uint32_t* meta_words = nullptr;  // packed metadata
   float* w_dense = nullptr;        // dense coefficient cube (CUDA-core engine)

@@ -139,6 +139,44 @@ def test_run_host_matches_device_run():
     plan.close()
 
 
+def test_repeated_runs_replay_a_graph_with_the_same_results():
+    # spider_run captures a repeated call as a CUDA graph (second call) and
+    # replays it (third call on); results must not change, for several
+    # cached (grids, steps) keys, across an engine switch and back, and when
+    # the input grid's contents change between replays
+    g = si.rng(16, 0)
+    u0 = si.grid((130, 260), -1, 1, g)
+    w = si.normalised_coeffs(2, 2, "box", g)
+    plan = spider.Plan(w, u0.shape, "box", "tf32")
+    plan.set_steps_per_pass(2)
+    a = torch.from_numpy(u0).cuda()
+    outs = [torch.empty_like(a) for _ in range(2)]
+    ref = {s: gpu_run(u0, w, s, "box", "tf32", "sparse_tc", 2) for s in (1, 5)}
+    for _ in range(4):
+        for o in outs:
+            for s in (1, 5):
+                o.fill_(float("nan"))
+                plan.run(a, o, s)
+                torch.cuda.synchronize()
+                assert np.array_equal(o.cpu().numpy(), ref[s]), s
+    plan.set_engine("dense_tc")
+    dense = gpu_run(u0, w, 5, "box", "tf32", "dense_tc", 2)
+    for _ in range(3):
+        plan.run(a, outs[0], 5)
+        torch.cuda.synchronize()
+        assert np.array_equal(outs[0].cpu().numpy(), dense)
+    plan.set_engine("sparse_tc")
+    u1 = si.grid(u0.shape, -1, 1, g)
+    ref1 = gpu_run(u1, w, 5, "box", "tf32", "sparse_tc", 2)
+    for k in range(3):
+        a.copy_(torch.from_numpy(u1 if k % 2 == 0 else u0))
+        plan.run(a, outs[1], 5)
+        plan.sync()
+        torch.cuda.synchronize()
+        assert np.array_equal(outs[1].cpu().numpy(), ref1 if k % 2 == 0 else ref[5])
+    plan.close()
+
+
 def test_repeat_runs_are_bitwise_identical():
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(512, 1024))
     a = gpu_run(u0, w, 5)
