@@ -83,7 +83,9 @@ typedef enum { SPIDER_ENGINE_SPARSE_TC = 0, SPIDER_ENGINE_DENSE_TC = 1, SPIDER_E
  *            must be < 2^40.
  *  shape     SPIDER_STAR: only on-axis coefficients may be non-zero;
  *            SPIDER_BOX: any.
- *  radius    1..3.
+ *  radius    1..3; 4..7 for 1-D and 2-D stencils in TF32 with the sparse
+ *            engine (windows of 16 outputs, the paper's L = 2r + 2 <= 16
+ *            layout, Sec. 3.1), one time step per pass.
  *  coeffs    dense (2r+1)^ndim float32 cube, row-major [dz][dy][dx], each
  *            offset running -r..r; host memory, copied; finite values only.
  *  prec      see spider_precision.
@@ -91,13 +93,14 @@ typedef enum { SPIDER_ENGINE_SPARSE_TC = 0, SPIDER_ENGINE_DENSE_TC = 1, SPIDER_E
  *            spider_plan_destroy).
  * Errors: SPIDER_ERR_INVALID (bad ndim/extents/radius/NULL, non-finite
  * coefficients, non-zero off-axis coefficient for a star),
- * SPIDER_ERR_UNSUPPORTED (radius > 3). */
+ * SPIDER_ERR_UNSUPPORTED (radius > 7, or radius 4..7 for 3-D or a split
+ * precision). */
 spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape shape, int radius,
                                  const float* coeffs, spider_precision prec, spider_plan* out);
 
 /* Selects the kernel the plan runs (default SPIDER_ENGINE_SPARSE_TC).  The
  * comparators support SPIDER_TF32 (DENSE_TC) and plain FP32 (CUDA_CORE,
- * precision ignored). */
+ * precision ignored), radius 1..3 (SPIDER_ERR_UNSUPPORTED otherwise). */
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
 /* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4
@@ -270,7 +273,8 @@ spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out);
 /* Submits a job.  `plan` is copied (the caller may destroy it afterwards).
  * host_in: host grid of the plan's extents, copied before return.
  * err_target: relative L2 error the caller accepts; <= 1e-4 selects a split
- * precision, otherwise the plan's precision.  *ticket identifies the job.
+ * precision (radius <= 3; the wide layout of radius 4..7 stays TF32),
+ * otherwise the plan's precision.  *ticket identifies the job.
  * SPIDER_ERR_OOM if the job alone exceeds the budget; SPIDER_ERR_BUSY if the
  * queue is full. */
 spider_status spider_submit(spider_server server, spider_plan plan, const float* host_in, int64_t steps,

@@ -114,6 +114,7 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
 int max_steps_per_pass(const spider_plan_t* p) {
+  if (p->wide()) return 1;
   if (p->ndim == 2) return 4;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
   if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
@@ -255,7 +256,9 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
   if (ndim < 1 || ndim > 3) return fail(SPIDER_ERR_INVALID, "ndim must be 1, 2 or 3");
   if (!extents || !coeffs) return fail(SPIDER_ERR_INVALID, "extents/coeffs is NULL");
   if (radius < 1) return fail(SPIDER_ERR_INVALID, "radius must be >= 1");
-  if (radius > kMaxR) return fail(SPIDER_ERR_UNSUPPORTED, "radius > 3 is not built");
+  if (radius > kMaxRWide) return fail(SPIDER_ERR_UNSUPPORTED, "radius > 7 is not built");
+  if (radius > kMaxR && (ndim > 2 || (prec != SPIDER_TF32 && prec != SPIDER_AUTO)))
+    return fail(SPIDER_ERR_UNSUPPORTED, "radius 4..7 is built for 1-D and 2-D stencils in TF32");
   if (shape != SPIDER_STAR && shape != SPIDER_BOX) return fail(SPIDER_ERR_INVALID, "bad shape");
   if (prec < SPIDER_TF32 || prec > SPIDER_AUTO) return fail(SPIDER_ERR_INVALID, "bad precision");
   long double total = 1;
@@ -308,6 +311,8 @@ spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
   if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_CUDA_CORE) return fail(SPIDER_ERR_INVALID, "bad engine");
   if (engine == SPIDER_ENGINE_DENSE_TC && p->prec != SPIDER_TF32)
     return fail(SPIDER_ERR_UNSUPPORTED, "the dense tensor-core comparator runs TF32 only");
+  if (engine != SPIDER_ENGINE_SPARSE_TC && p->r > kMaxR)
+    return fail(SPIDER_ERR_UNSUPPORTED, "radius 4..7 is built for the sparse tensor-core engine only");
   std::lock_guard<std::mutex> lock(p->mu);
   if (p->engine == engine) return SPIDER_OK;
   p->engine = engine;

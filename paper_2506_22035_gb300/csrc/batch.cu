@@ -282,7 +282,8 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
   std::vector<int> queued, direct;
   for (int i = 0; i < n; ++i) {
     spider_plan_t* p = plans[i];
-    const bool ok = p->ndim == 2 && p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec == SPIDER_TF32 && steps[i] > 0;
+    const bool ok = p->ndim == 2 && p->r <= kMaxR && p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec == SPIDER_TF32 &&
+                    steps[i] > 0;
     (ok ? queued : direct).push_back(i);
   }
   if (!queued.empty()) {

@@ -203,7 +203,8 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
   if (!s || !plan || !host_in || !ticket || steps < 0 || !(err_target > 0))
     return fail(SPIDER_ERR_INVALID, "bad arguments");
   // a private plan: split precision for tight error targets
-  const spider_precision prec = err_target <= 1e-4 ? SPIDER_F16X2 : plan->prec;
+  // (the wide layout of radius 4..7 is TF32 only)
+  const spider_precision prec = (err_target <= 1e-4 && plan->r <= kMaxR) ? SPIDER_F16X2 : plan->prec;
   spider_plan copy = nullptr;
   spider_status st = spider_plan_create(plan->ndim, plan->extents, plan->shape, plan->r, plan->w.data(), prec, &copy);
   if (st != SPIDER_OK) return st;

@@ -19,8 +19,8 @@
 // tiles where that place changes the arithmetic: 8-point segments along x
 // (the output index inside a segment selects the A row), and row pairs along
 // y for the split precisions, whose k32 products take two input rows at
-// once.  Slab boundaries and ghost depths are therefore multiples of 8 (1-D)
-// or 2 (2-D).
+// once.  Slab boundaries and ghost depths are therefore multiples of 8 (1-D;
+// 16 for the 16-point segments of the wide layout) or 2 (2-D).
 //
 // On a machine with one GPU per slab each slab would live on its own device
 // and the exchange would be a peer copy; here every slab is on the current
@@ -97,7 +97,8 @@ spider_status spider_domain_create(spider_plan plan, int parts, int steps_per_ex
   d->axis = plan->extents[0];
   d->plane = plan->points() / d->axis;
   d->exchange = steps_per_exchange > 0 ? steps_per_exchange : plan->steps_per_pass;
-  const int64_t align = plan->ndim == 1 ? 8 : plan->ndim == 2 ? 2 : 1;
+  // x slabs keep 8-point segments (16-point segments in the wide layout)
+  const int64_t align = plan->ndim == 1 ? (plan->wide() ? 16 : 8) : plan->ndim == 2 ? 2 : 1;
   const int64_t need = (int64_t)d->exchange * plan->r;
   d->ghost = parts > 1 ? (need + align - 1) / align * align : 0;
   if (parts > d->axis) return fail(SPIDER_ERR_INVALID, "more parts than planes");

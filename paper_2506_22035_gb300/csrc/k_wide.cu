@@ -1,0 +1,18 @@
+// Dispatch of the wide layout (radius 4..7 in 1-D and 2-D, radius 1..3 in
+// 1-D; sparse TF32).
+#include "launch_impl.cuh"
+
+namespace spider {
+cudaError_t launch_wide_sp_tf32(int cls, int r, const LaunchCtx& ctx) {
+  switch (r) {
+    case 1: return launch_wide_r<1>(cls, ctx);
+    case 2: return launch_wide_r<2>(cls, ctx);
+    case 3: return launch_wide_r<3>(cls, ctx);
+    case 4: return launch_wide_r<4>(cls, ctx);
+    case 5: return launch_wide_r<5>(cls, ctx);
+    case 6: return launch_wide_r<6>(cls, ctx);
+    case 7: return launch_wide_r<7>(cls, ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
+}  // namespace spider

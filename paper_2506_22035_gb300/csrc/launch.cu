@@ -56,6 +56,7 @@ int device_sm_count() {
 cudaError_t launch_step(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
   const int cls = p->ndim;
+  if (p->wide()) return launch_wide_sp_tf32(cls, p->r, ctx);
   switch (p->engine) {
     case SPIDER_ENGINE_CUDA_CORE: return launch_cuda_core(cls, p->r, ctx);
     case SPIDER_ENGINE_DENSE_TC: return launch_dense_tf32(cls, p->r, ctx);

@@ -10,6 +10,7 @@
 #include "stencil_kernels.cuh"
 #include "stream3d_fused_kernels.cuh"
 #include "stream3d_kernels.cuh"
+#include "wide_kernels.cuh"
 
 namespace spider {
 
@@ -391,6 +392,69 @@ cudaError_t launch_fused3d_mode(int r, int T, const LaunchCtx& ctx) {
     case 4: return launch_fused3d_t<MODE, 4>(ctx);
     default: return cudaErrorNotSupported;
   }
+}
+
+
+// ---- wide layout, radius 4..7 ---------------------------------------------
+template <class C, bool RIN>
+cudaError_t launch_wide_k(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  auto kern = wide_step_kernel<C, RIN>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = 1;
+  a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
+  a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  a.use_tma = make_tensor_map(&map, ctx.src, p->nx, p->ny, 1, C::SX, C::SY, 1) ? 1 : 0;
+  const long long ntiles = (long long)a.tiles_x * a.tiles_y;
+  if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
+  return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
+}
+
+// 2-D: 8 warps x 8 rows x 128 columns, registers for 2 CTAs per SM; 1-D: one
+// warp per 128 points.
+template <int R>
+cudaError_t launch_wide_r(int cls, const LaunchCtx& ctx) {
+  if (cls == 2) {
+    if constexpr (R <= kMaxR) return cudaErrorNotSupported;  // 2-D radius 1..3: the 8-output layout
+    using C = WideCfg<R, R, 8, 8, 2>;
+    return ctx.in_tf32 ? launch_wide_k<C, false>(ctx) : launch_wide_k<C, true>(ctx);
+  }
+  if (cls == 1) {
+    return ctx.in_tf32 ? launch_wide_k<WideCfg<0, R, 1, 1>, false>(ctx) : launch_wide_k<WideCfg<0, R, 1, 1>, true>(ctx);
+  }
+  return cudaErrorNotSupported;
 }
 
 }  // namespace spider

@@ -175,15 +175,16 @@ uint32_t f32_bits(float x) {
 // with q in {0,1} hold row g pairs 4q..4q+3 in bits 0-15 and row g+8 in bits
 // 16-31, one nibble per pair: 0b0100 keeps the first element, 0b1110 the
 // second.
-void pack_tf32_sparse(const WindowMatrix& A, uint32_t* words /*32x4*/, uint32_t* meta /*32*/) {
+// `K` is in MMA K order (column k = K index).
+void pack_tf32_sparse_k(const WindowMatrix& K, uint32_t* words /*32x4*/, uint32_t* meta /*32*/) {
   float cval[16][8];
   int cidx[16][8];
   for (int m = 0; m < 16; ++m) {
     for (int c = 0; c < 8; ++c) {
-      const int p0 = phi_tf32(2 * c), p1 = phi_tf32(2 * c + 1);
-      if (A.mask[m][p0] && A.mask[m][p1]) throw std::runtime_error("internal: pair not 1:2");
-      if (A.mask[m][p1]) { cidx[m][c] = 1; cval[m][c] = A.v[m][p1]; }
-      else { cidx[m][c] = 0; cval[m][c] = A.mask[m][p0] ? A.v[m][p0] : 0.f; }
+      const int p0 = 2 * c, p1 = 2 * c + 1;
+      if (K.mask[m][p0] && K.mask[m][p1]) throw std::runtime_error("internal: pair not 1:2");
+      if (K.mask[m][p1]) { cidx[m][c] = 1; cval[m][c] = K.v[m][p1]; }
+      else { cidx[m][c] = 0; cval[m][c] = K.mask[m][p0] ? K.v[m][p0] : 0.f; }
     }
   }
   for (int lane = 0; lane < 32; ++lane) {
@@ -203,6 +204,36 @@ void pack_tf32_sparse(const WindowMatrix& A, uint32_t* words /*32x4*/, uint32_t*
     }
     meta[lane] = e;
   }
+}
+
+// `A` is in window coordinates; its K order is taken through phi_tf32.
+void pack_tf32_sparse(const WindowMatrix& A, uint32_t* words /*32x4*/, uint32_t* meta /*32*/) {
+  WindowMatrix K;
+  for (int m = 0; m < 16; ++m)
+    for (int k = 0; k < 16; ++k) {
+      K.v[m][k] = A.v[m][phi_tf32(k)];
+      K.mask[m][k] = A.mask[m][phi_tf32(k)];
+    }
+  pack_tf32_sparse_k(K, words, meta);
+}
+
+// Wide layout (radius 4..7): K half h of kernel row kr (dy = kr - ry) in K
+// order.  Row m is output m of a 16-output segment, window position
+// phi_wide(h, k) is input x = x0 - 8 + position; entry w[dy][dx] with
+// dx = position - 8 - m when |dx| <= r.  The band of 2r + 1 <= 15 positions
+// never holds both p and p + 16, so every pair is 1:2 (Sec. 3.1.2 with
+// L = 16, the paper's worked example for r = 7).
+WindowMatrix wide_matrix(const spider_plan_t* p, const std::vector<float>& coeffs, int kr, int h) {
+  WindowMatrix K;
+  const int wx = 2 * p->rx + 1;
+  for (int m = 0; m < 16; ++m)
+    for (int k = 0; k < 16; ++k) {
+      const int dx = phi_wide(h, k) - kWideHalo - m;
+      const bool in = dx >= -p->rx && dx <= p->rx;
+      K.mask[m][k] = in;
+      K.v[m][k] = in ? coeffs[(size_t)kr * wx + (dx + p->rx)] : 0.f;
+    }
+  return K;
 }
 
 // Dense TF32 m16n8k8, two K halves: a0 (g, q), a1 (g+8, q), a2 (g, q+4),
@@ -285,6 +316,19 @@ spider_status build_operands(spider_plan_t* p) {
   p->meta_words.clear();
   try {
     const std::vector<float> w_tf32 = tf32_sum_preserving(p->w);
+    if (p->wide()) {
+      // wide layout: [kernel row][K half][lane] (sparse TF32 only)
+      const int nkr = 2 * p->ry + 1;
+      p->n_arows = nkr;
+      p->n_combos = 2 * nkr;
+      p->a_words.resize((size_t)p->n_combos * 128);
+      p->meta_words.resize((size_t)p->n_combos * 32);
+      for (int kr = 0; kr < nkr; ++kr)
+        for (int h = 0; h < 2; ++h)
+          pack_tf32_sparse_k(wide_matrix(p, w_tf32, kr, h), &p->a_words[(size_t)(2 * kr + h) * 128],
+                             &p->meta_words[(size_t)(2 * kr + h) * 32]);
+      return SPIDER_OK;
+    }
     if (p->engine == SPIDER_ENGINE_CUDA_CORE) {
       p->n_combos = 0;
       return SPIDER_OK;

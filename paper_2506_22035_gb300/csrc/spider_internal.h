@@ -29,6 +29,17 @@ constexpr int kSeg = 8;          // L: outputs per segment
 constexpr int kWin = 16;         // 2L: input window per segment
 constexpr int kHaloX = 4;        // window starts 4 points left of the segment
 constexpr int kMaxR = 3;
+// Radii 4..7 (1-D and 2-D, sparse TF32) use the wide layout: L = 16 outputs
+// per segment, 32-wide windows starting 8 points left of the segment, two
+// k16 MMAs per kernel row (see wide_kernels.cuh and plan.cu).
+constexpr int kMaxRWide = 7;
+constexpr int kWideHalo = 8;
+// Window position of K index k in K half h of the wide layout: the 1:2 pair
+// (2c, 2c+1) lands on positions p and p + 16, and lane q's four B values
+// (k = q + 4i) are four consecutive positions.
+__host__ __device__ constexpr int phi_wide(int h, int k) {
+  return 8 * h + 4 * ((k % 4) >> 1) + 16 * ((k % 4) & 1) + k / 4;
+}
 
 // Fragment-aware strided permutation.  MMA K-index k of the TF32
 // m16n8k16 B fragment lives in lane q = k % 4, register i = k / 4; we place
@@ -93,6 +104,13 @@ struct spider_plan_t {
   std::mutex mu;
 
   int64_t points() const { return nz * ny * nx; }
+  // The wide layout (wide_kernels.cuh) serves radius 4..7 and every 1-D
+  // sparse TF32 plan (its 16-output segments fill both halves of M, where the
+  // 8-output layout would leave the second output row of a 1-D grid empty).
+  bool wide() const {
+    const bool sparse_tf32 = engine == SPIDER_ENGINE_SPARSE_TC && (prec == SPIDER_TF32 || prec == SPIDER_AUTO);
+    return r > spider::kMaxR || (ndim == 1 && sparse_tf32);
+  }
 };
 
 namespace spider {

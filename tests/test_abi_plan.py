@@ -58,7 +58,8 @@ def test_plan_argument_validation(lib):
     assert _create(lib, 4, (16, 16), 1, 1, ok) == _native.SPIDER_ERR_INVALID
     assert _create(lib, 2, (0, 16), 1, 1, ok) == _native.SPIDER_ERR_INVALID
     assert _create(lib, 2, (16, 16), 1, 0, ok) == _native.SPIDER_ERR_INVALID
-    assert _create(lib, 2, (16, 16), 1, 4, np.ones((9, 9), np.float32)) == _native.SPIDER_ERR_UNSUPPORTED
+    assert _create(lib, 2, (16, 16), 1, 4, np.ones((9, 9), np.float32)) == _native.SPIDER_OK  # wide layout
+    assert _create(lib, 2, (16, 16), 1, 8, np.ones((17, 17), np.float32)) == _native.SPIDER_ERR_UNSUPPORTED
     bad = ok.copy()
     bad[0, 0] = np.nan
     assert _create(lib, 2, (16, 16), 1, 1, bad) == _native.SPIDER_ERR_INVALID
@@ -148,7 +149,7 @@ def tf32(x):
     return b.view(np.float32)
 
 
-@pytest.mark.parametrize("ndim,r", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2), (1, 3)])
+@pytest.mark.parametrize("ndim,r", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2)])
 def test_tf32_operands_decode_to_banded_kernel_rows(ndim, r):
     gen = np.random.default_rng(100 + r)
     w = gen.standard_normal((2 * r + 1,) * ndim).astype(np.float32)
@@ -247,7 +248,7 @@ def _slabs(dom):
 
 
 @pytest.mark.parametrize("extents,r,E,parts,align", [((300, 520), 3, 2, 3, 2), ((301, 64), 1, 3, 4, 2),
-                                                      ((1000,), 2, 1, 3, 8), ((20, 33, 70), 1, 3, 2, 1),
+                                                      ((1000,), 2, 1, 3, 16), ((20, 33, 70), 1, 3, 2, 1),
                                                       ((64, 64), 2, 4, 1, 2)])
 def test_domain_layout(lib, extents, r, E, parts, align):
     # host logic of the slab decomposition: owned ranges tile the slowest
@@ -311,3 +312,96 @@ def test_steps_per_pass_where_fusion_is_built(lib):
     with pytest.raises(spider.SpiderError):
         p.set_steps_per_pass(2)
     p.close()
+
+
+def phi_wide(h, k):
+    """Wide layout (radius 4..7): window position of K index k in K half h;
+    the 1:2 pair (2c, 2c+1) lands on positions p and p + 16."""
+    return 8 * h + 4 * ((k % 4) >> 1) + 16 * ((k % 4) & 1) + k // 4
+
+
+def decode_k_order(words, meta):
+    """16 x 16 matrix in MMA K order from one sparse TF32 A operand."""
+    comp = np.zeros((16, 8), np.float32)
+    idx = np.full((16, 8), -1)
+    for lane in range(32):
+        g, q = divmod(lane, 4)
+        comp[g, q], comp[g + 8, q], comp[g, q + 4], comp[g + 8, q + 4] = words[lane].view(np.float32)
+        if q < 2:
+            for i in range(4):
+                for half, row in ((0, g), (16, g + 8)):
+                    nib = (int(meta[lane]) >> (half + 4 * i)) & 0xF
+                    assert nib in (0x4, 0xE)
+                    idx[row, 4 * q + i] = 0 if nib == 0x4 else 1
+    K = np.zeros((16, 16), np.float32)
+    for m in range(16):
+        for c in range(8):
+            K[m, 2 * c + idx[m, c]] += comp[m, c]
+    return K
+
+
+def test_wide_layout_pairs_are_16_apart_and_lane_loads_contiguous():
+    for h in (0, 1):
+        pos = [phi_wide(h, k) for k in range(16)]
+        assert sorted(pos) == sorted(set(pos))
+        for c in range(8):
+            assert pos[2 * c + 1] - pos[2 * c] == 16
+        for q in range(4):
+            assert [pos[q + 4 * i] for i in range(4)] == list(range(pos[q], pos[q] + 4))
+    assert sorted(phi_wide(h, k) for h in (0, 1) for k in range(16)) == list(range(32))
+    # no band of 2r + 1 <= 15 positions holds both members of a pair
+    for r in range(4, 8):
+        for start in range(0, 32 - 2 * r):
+            band = set(range(start, start + 2 * r + 1))
+            for h in (0, 1):
+                for c in range(8):
+                    assert not ({phi_wide(h, 2 * c), phi_wide(h, 2 * c + 1)} <= band)
+
+
+@pytest.mark.parametrize("ndim,r", [(2, 4), (2, 5), (2, 7), (1, 1), (1, 3), (1, 6), (1, 7)])
+def test_wide_operands_decode_to_banded_kernel_rows(ndim, r):
+    # radius 4..7, and every 1-D radius, use the wide layout
+    gen = np.random.default_rng(200 + r)
+    w = gen.standard_normal((2 * r + 1,) * ndim).astype(np.float32)
+    p = spider.Plan(w, (16,) * ndim, "box", "tf32")
+    words, meta = p.operands()
+    nkr = 2 * r + 1 if ndim == 2 else 1
+    w2 = w.reshape((nkr, 2 * r + 1))
+    assert words.size == nkr * 2 * 128 and meta.size == nkr * 2 * 32
+    words = words.reshape(nkr, 2, 32, 4)
+    meta = meta.reshape(nkr, 2, 32)
+    used = np.zeros_like(w2)
+    for kr in range(nkr):
+        win = np.zeros((16, 32), np.float32)  # row m: output m of the segment; column: window position
+        for h in (0, 1):
+            K = decode_k_order(words[kr, h], meta[kr, h])
+            for k in range(16):
+                win[:, phi_wide(h, k)] += K[:, k]
+        used[kr] = win[0, 8 - r:9 + r]
+        exp = np.zeros((16, 32), np.float32)
+        for m in range(16):
+            for pos in range(32):
+                dx = pos - 8 - m
+                if abs(dx) <= r:
+                    exp[m, pos] = used[kr, dx + r]
+        assert np.array_equal(win, exp), kr
+    bits = w2.view(np.uint32) & np.uint32(0xFFFFE000)
+    assert np.all((used == bits.view(np.float32)) | (used == (bits + np.uint32(0x2000)).view(np.float32)))
+    p.close()
+
+
+def test_wide_radius_limits(lib):
+    def create(nd, r, prec="tf32"):
+        return spider.Plan(np.full((2 * r + 1,) * nd, 0.01, np.float32), (32,) * nd, "box", prec)
+    for nd, r in ((1, 4), (2, 7)):
+        p = create(nd, r)
+        with pytest.raises(spider.SpiderError) as e:
+            p.set_engine("dense_tc")
+        assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
+        with pytest.raises(spider.SpiderError):
+            p.set_steps_per_pass(2)
+        p.close()
+    for nd, r, prec in ((3, 4, "tf32"), (2, 8, "tf32"), (2, 5, "f16x2"), (1, 4, "bf16x3")):
+        with pytest.raises(spider.SpiderError) as e:
+            create(nd, r, prec)
+        assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED

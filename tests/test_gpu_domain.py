@@ -46,6 +46,8 @@ def _run_both(u0, w, steps, shape, prec, engine, T, parts, E):
     ((200, 264), 2, "tf32", "dense_tc", 2, 2, 2, 5),
     ((200, 264), 1, "tf32", "cuda_core", 1, 3, 2, 5),
     ((4000,), 2, "tf32", "sparse_tc", 1, 3, 3, 8),          # 1-D, x slabs on 8-point segments
+    ((4000,), 6, "tf32", "sparse_tc", 1, 3, 2, 5),          # 1-D radius 6: 16-point segments
+    ((300, 264), 5, "tf32", "sparse_tc", 1, 2, 2, 5),       # 2-D radius 5
     ((24, 40, 72), 1, "tf32", "sparse_tc", 1, 2, 2, 5),     # 3-D z slabs, z-streaming kernel
     ((40, 24, 72), 1, "tf32", "sparse_tc", 2, 2, 2, 7),     # 3-D fused passes
     ((20, 33, 70), 2, "f16x2", "sparse_tc", 1, 2, 1, 3),    # 3-D, unaligned rows

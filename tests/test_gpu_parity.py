@@ -316,6 +316,40 @@ def test_fused_3d_passes_match_single_steps(shape_kind, shape):
     check_close(single, oracle.stencil(u0, w, 7), ("sparse_tc", "tf32"))
 
 
+@pytest.mark.parametrize("r", [4, 5, 6, 7])
+@pytest.mark.parametrize("shape", [(150, 300), (67, 517), (1, 900), (2053,), (96,)])
+def test_wide_radius_integer_inputs_bit_exact(r, shape):
+    # radius 4..7: sparse {-1, 1} weights and a {-1, 0, 1} grid keep every
+    # intermediate below 2^11, so TF32 products and FP32 sums are exact
+    g = si.rng(17, r)
+    nd = len(shape)
+    w = np.zeros((2 * r + 1,) * nd, np.float32)
+    flat = w.reshape(-1)
+    pick = g.choice(flat.size, size=min(flat.size, 9), replace=False)
+    flat[pick] = g.choice([-1.0, 1.0], size=pick.size)
+    u0 = g.integers(-1, 2, size=shape).astype(np.float32)
+    got = gpu_run(u0, w, 2, "box", "tf32", "sparse_tc")
+    assert np.array_equal(got, oracle.stencil(u0, w, 2).astype(np.float32)), (r, shape)
+
+
+@pytest.mark.parametrize("r", [4, 7])
+@pytest.mark.parametrize("shape", [(300, 520), (131, 259), (5000,)])
+def test_wide_radius_parity_and_chained_calls(r, shape):
+    g = si.rng(18, r)
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(len(shape), r, "box", g)
+    got = gpu_run(u0, w, 6, "box", "tf32", "sparse_tc")
+    check_close(got, oracle.stencil(u0, w, 6), ("sparse_tc", "tf32"))
+    u = u0
+    for _ in range(6):
+        u = gpu_run(u, w, 1, "box", "tf32", "sparse_tc")
+    assert np.array_equal(got, u)
+    if len(shape) == 2:
+        star_w = si.normalised_coeffs(2, r, "star", g)
+        check_close(gpu_run(u0, star_w, 4, "star", "tf32", "sparse_tc"), oracle.stencil(u0, star_w, 4),
+                    ("sparse_tc", "tf32"))
+
+
 @pytest.mark.parametrize("T", [2, 3, 4])
 def test_fused_parity_with_oracle(T):
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
