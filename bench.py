@@ -6,7 +6,7 @@ step of it (e.g. 100 steps of a 7x7 box stencil on an 8192^2 grid), with the
 input grid resident in HBM.  GStencil/s = grid points x time steps / seconds
 / 1e9.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d]
+  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d|batched|serving|sweep]
                   [--precision tf32|f16x2|bf16x3] [--impl spider|reference] [--accuracy]
 
 Under torchrun every rank runs the whole workload on its own GPU (independent
@@ -51,12 +51,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spider", choices=["spider", "reference"])
-    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS) + ["batched", "serving", "sweep"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
     ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
                     help="time steps fused per HBM pass (default: chosen by spider_plan_autotune)")
     ap.add_argument("--tile-variant", type=int, default=None)
+    ap.add_argument("--radius", type=int, default=None,
+                    help="override the workload's stencil radius (box2d: 1..7)")
     ap.add_argument("--extents", type=int, nargs="+", default=None,
                     help="override the grid size (same distributions; for profiling runs)")
     ap.add_argument("--jobs", type=int, default=None, help="batched: use the first N of the 64 jobs")
@@ -108,7 +110,8 @@ def measured_peaks():
 # The files that define the stencil kernels, their geometry and their launch
 # configuration: a change to any of them invalidates recorded ncu counters.
 KERNEL_SOURCES = ("device_common.cuh", "fused_kernels.cuh", "launch.cu", "launch.h", "launch_impl.cuh",
-                  "spider_internal.h", "stencil_kernels.cuh", "stream3d_fused_kernels.cuh", "stream3d_kernels.cuh")
+                  "spider_internal.h", "stencil_kernels.cuh", "stream3d_fused_kernels.cuh", "stream3d_kernels.cuh",
+                  "wide_kernels.cuh")
 
 
 def kernel_source_sha() -> str:
@@ -302,6 +305,9 @@ def run_spider(a):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     wl = WORKLOADS[a.workload]
+    if a.radius:
+        # another radius of the same stencil family (e.g. the wide layout, r = 4..7)
+        wl = dataclasses.replace(wl, r=a.radius, name=wl.name.replace(f"-r{wl.r}-", f"-r{a.radius}-"))
     if a.extents:
         wl = dataclasses.replace(wl, extents=tuple(a.extents), name=f"{wl.name.split('-')[0]}-r{wl.r}-"
                                  + "x".join(map(str, a.extents)))
@@ -358,6 +364,8 @@ def run_spider(a):
         achieved = alg_bytes / per_launch_s / 1e9
         if wl.ndim == 3:
             kernel = "stream3d_fused_kernel" if T > 1 else "stream3d_kernel"
+        elif wl.ndim == 1 or wl.r > 3:
+            kernel = "wide_step_kernel"
         else:
             kernel = "fused_step_kernel" if T > 1 else "stencil_step_kernel"
         # every tile variant of a given T loads the same boxes and writes the
@@ -404,7 +412,11 @@ def run_spider(a):
         for eng, prec in variants:
             if (eng, prec) == (a.engine, a.precision):
                 continue
-            p2 = spider.Plan(w, wl.extents, wl.shape, prec, eng)
+            try:
+                p2 = spider.Plan(w, wl.extents, wl.shape, prec, eng)
+            except spider.SpiderError as err:  # e.g. radius 4..7 exists for sparse TF32 only
+                comps[f"{eng}/{prec}"] = {"value": None, "unsupported": str(err)}
+                continue
             t2, v2 = p2.autotune(a_in, b_out, wl.steps, stream)   # each comparator at its own best setting
             iters = max(3, a.steps // 10)
             for _ in range(2):
@@ -496,6 +508,64 @@ def run_batched(a):
     return 0
 
 
+SWEEP_SIDES = (512, 1024, 2048, 4096, 8192, 10240)
+
+
+def run_sweep(a):
+    """Size sweep and engine ablation (the paper's 512^2 ... 10240^2 trend
+    study and its TC -> SpTC ablation on Box-2D2R): 2-D box stencils of radius
+    2 and 3, 100 time steps per run, every side in SWEEP_SIDES, each engine
+    (sparse TC, dense TC on the same banded K, CUDA cores) at the steps per
+    pass and tile variant its autotuner picks.  Prints one JSON line whose
+    "sweep" list holds one record per (radius, side, engine)."""
+    import torch
+    import paper_2506_22035_gb300 as spider
+    from paper_2506_22035_gb300 import build as _b
+    _b.build()
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    steps_per_run = 100
+    sides = [int(x) for x in a.extents] if a.extents else list(SWEEP_SIDES)
+    records = []
+    for r in (2, 3):
+        gen = si.rng(30, r)
+        w = si.normalised_coeffs(2, r, "box", gen)
+        for n in sides:
+            u0 = si.grid((n, n), -1.0, 1.0, gen)
+            a_in = torch.from_numpy(u0).to(dev)
+            b_out = torch.empty_like(a_in)
+            fl = None if 4 * n * n > L2_BYTES else flush
+            for engine in ("sparse_tc", "dense_tc", "cuda_core"):
+                plan = spider.Plan(w, (n, n), "box", "tf32", engine)
+                T, v = plan.autotune(a_in, b_out, steps_per_run, stream)
+                for _ in range(max(3, a.warmup)):
+                    plan.run(a_in, b_out, steps_per_run, stream)
+                iters = max(2, min(a.steps, int(2e11 // (n * n * steps_per_run)) or 2))
+                dt = time_runs(plan, a_in, b_out, steps_per_run, iters, fl, stream)
+                plan.close()
+                records.append({"radius": r, "side": n, "engine": engine, "steps_per_pass": T, "tile_variant": v,
+                                "gstencil_s": n * n * steps_per_run * iters / dt / 1e9,
+                                "us_per_run": dt / iters * 1e6})
+            del a_in, b_out
+    sp = {(x["radius"], x["side"]): x["gstencil_s"] for x in records if x["engine"] == "sparse_tc"}
+    for x in records:
+        x["sparse_tc_speedup"] = sp[(x["radius"], x["side"])] / x["gstencil_s"]
+    best = max(x["gstencil_s"] for x in records if x["engine"] == "sparse_tc")
+    line = {"metric": "GStencil/s", "value": best, "unit": "GStencil/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+            "data": "synthetic",
+            "config": {"workload": "sweep: 2-D box r = 2, 3, sides " + ",".join(map(str, sides)) +
+                                   ", 100 time steps per run, each engine autotuned",
+                       "l2": "flushed between timed runs for grids smaller than L2"},
+            "sweep": records}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(a):
     """Poisson arrivals (200 jobs/s) of mixed 2-D/3-D stencil jobs submitted to
     the continuous-batching server; a bounded prefix of the arrival sequence
@@ -563,6 +633,8 @@ def main():
         return run_batched(a)
     if a.workload == "serving":
         return run_serving(a)
+    if a.workload == "sweep":
+        return run_sweep(a)
     return run_spider(a)
 
 
