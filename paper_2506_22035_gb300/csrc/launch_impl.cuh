@@ -442,8 +442,55 @@ cudaError_t launch_wide_k(const LaunchCtx& ctx) {
   return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
 
-// 2-D: 8 warps x 8 rows x 128 columns, registers for 2 CTAs per SM; 1-D: one
-// warp per 128 points.
+// 1-D: tiles of 16 rows of 128 points (8 warps x 2 rows), chunks loaded by
+// TMA through a view of the array as rows of 8 floats.
+template <class C, bool RIN>
+cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  auto kern = wide1d_kernel<C, RIN>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = 1;
+  a.nz = 1;
+  a.tiles_x = (int)((p->nx + C::NT - 1) / C::NT);
+  a.tiles_y = 1;
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  // the array as rows of 8 floats (needs a length that is a multiple of 8)
+  a.use_tma = (p->nx % 8 == 0 && make_tensor_map(&map, ctx.src, 8, p->nx / 8, 1, 8, C::kBoxRows, 1)) ? 1 : 0;
+  const int grid = (int)std::min<long long>(a.tiles_x, (long long)occ * ctx.sms);
+  return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
+}
+
+// 2-D: 8 warps x 8 rows x 128 columns, registers for 2 CTAs per SM; 1-D:
+// tiles of 16 rows of 128 points.
 template <int R>
 cudaError_t launch_wide_r(int cls, const LaunchCtx& ctx) {
   if (cls == 2) {
@@ -452,7 +499,8 @@ cudaError_t launch_wide_r(int cls, const LaunchCtx& ctx) {
     return ctx.in_tf32 ? launch_wide_k<C, false>(ctx) : launch_wide_k<C, true>(ctx);
   }
   if (cls == 1) {
-    return ctx.in_tf32 ? launch_wide_k<WideCfg<0, R, 1, 1>, false>(ctx) : launch_wide_k<WideCfg<0, R, 1, 1>, true>(ctx);
+    using C = Wide1DCfg<R, 2, 8>;
+    return ctx.in_tf32 ? launch_wide1d_k<C, false>(ctx) : launch_wide1d_k<C, true>(ctx);
   }
   return cudaErrorNotSupported;
 }

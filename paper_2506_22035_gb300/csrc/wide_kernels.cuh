@@ -190,3 +190,129 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
 }
 
 }  // namespace spider
+
+namespace spider {
+
+// 1-D grids in the wide layout, several 128-point rows per warp.  The array
+// is taken as consecutive rows of 128 points; a tile of BY rows is one
+// contiguous chunk [X0 - 8, X0 + 128 BY + 8) in shared memory, so the window
+// of a row's last segment runs into the next row's first points, which are
+// its true neighbours.  The chunk is loaded by TMA through a 2-D view of the
+// array as rows of 8 floats, zero outside the array: two boxes of 8 BY + 4
+// such rows, so that the second box starts on a 128-byte boundary of shared
+// memory (48 floats beyond the chunk are loaded and not used).  Arrays whose
+// length is not a multiple of 8 load the chunk with cp.async.
+template <int RX_, int H_, int NW_>
+struct Wide1DCfg {
+  static constexpr int RZ = 0, RY = 0, RX = RX_, H = H_, NW = NW_;
+  static constexpr int kMinBlocks = 1;
+  static constexpr int SX = 128;                  // row pitch in shared memory (no halo columns)
+  static constexpr int BY = NW * H, NT = BY * SX;  // rows and points per tile
+  static constexpr int kChunk = NT + 2 * kWideHalo;  // points the tile reads
+  static constexpr int kBoxRows = 8 * BY + 4;          // rows of 8 floats per TMA box (two boxes)
+  static constexpr int kThreads = NW * 32;
+  static constexpr int kStageBytes = 2 * kBoxRows * 8 * 4;
+  static constexpr int kStageStride = (kStageBytes + 1023) / 1024 * 1024;
+  static constexpr int kSmemBytes = 2 * kStageStride + 1024 + 64;
+  static constexpr int NKR = 1;
+  static_assert(2 * kBoxRows * 8 >= kChunk && (kBoxRows * 32) % 128 == 0 && kBoxRows <= 256, "TMA boxes");
+  static_assert(RX >= 1 && RX <= kMaxRWide, "wide layout radius");
+};
+
+template <class C, bool RIN>
+__global__ void __launch_bounds__(C::kThreads)
+    wide1d_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base_u32 = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
+  auto stage = [&](int s) { return reinterpret_cast<float*>(smem + s * C::kStageStride); };
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * C::kStageStride);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wy = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int64_t n = args.nx;
+  const int ntiles = args.tiles_x;
+  const bool use_tma = args.use_tma != 0;
+  auto issue = [&](int t, int s) {
+    // chunk start X0 - 8 is a multiple of 8: row (X0 - 8) / 8 of the 8-float view
+    const int row8 = (int)(((int64_t)t * C::NT - kWideHalo) / 8);
+    mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+    tma_load_3d(stage(s), &tmap, &full[s], 0, row8, 0);
+    tma_load_3d(stage(s) + C::kBoxRows * 8, &tmap, &full[s], 0, row8 + C::kBoxRows, 0);
+  };
+
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_mbar_init();
+  }
+  griddep_wait();  // see stencil_step_kernel
+  griddep_launch_dependents();
+  __syncthreads();
+  if (use_tma && tid == 0) {
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+  const int coff = 16 * g + phi_wide(0, q);
+
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    float* S = stage(s);
+    const int64_t x0 = (int64_t)t * C::NT;
+    if (use_tma) {
+      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+      if (!__syncthreads_and(ok)) break;
+    } else {
+      load_box_async(args.src, n, 1, 1, x0 - kWideHalo, 0, 0, C::kChunk, 1, 1, S, wy, C::kThreads / 32, lane);
+      __syncthreads();
+    }
+    if (RIN) {
+      for (int i = tid; i < C::kChunk; i += C::kThreads) S[i] = __uint_as_float(cvt_tf32(S[i]));
+      __syncthreads();
+    }
+    float acc[C::H][4];
+#pragma unroll
+    for (int i = 0; i < C::H; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    wide_groups<C, 0>(smem_u32(S + (wy * C::H) * C::SX + coff), args, lane, acc);
+    if (args.out_tf32) {
+#pragma unroll
+      for (int i = 0; i < C::H; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = __uint_as_float(cvt_tf32(acc[i][j]));
+    }
+    // row yy of this warp starts at point x0 + (wy H + yy) 128; output m of
+    // segment n sits 16 n + m further (fragment map as in wide_step_kernel)
+    const int64_t xw = x0 + (int64_t)(wy * C::H) * C::SX + 32 * q + g;
+    const bool interior = x0 + C::NT <= n;
+#pragma unroll
+    for (int yy = 0; yy < C::H; ++yy) {
+      float* o = args.dst + xw + yy * C::SX;
+      const int64_t xr = xw + yy * C::SX;
+      const int offs[4] = {0, 16, 8, 24};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (interior || xr + offs[j] < n) o[offs[j]] = acc[yy][j];
+    }
+
+    __syncthreads();  // every warp is done with stage s
+    if (use_tma && tid == 0) {
+      const int tn = t + 2 * (int)gridDim.x;
+      if (tn < ntiles) {
+        fence_proxy_async_smem();
+        issue(tn, s);
+      }
+    }
+  }
+  if (use_tma && tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int t = blockIdx.x + (it + k) * gridDim.x;
+      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+    }
+  }
+}
+
+}  // namespace spider
