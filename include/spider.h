@@ -104,8 +104,8 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
 /* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4
- * for 2-D stencils and for 3-D radius-1 plans with the sparse engine in TF32;
- * 1 otherwise.  Values the build does not support for the plan's stencil
+ * for 2-D stencils of radius 1..3, and with the sparse engine in TF32 for
+ * 3-D radius-1 and 1-D plans; 1 otherwise.  Values the build does not support for the plan's stencil
  * return SPIDER_ERR_UNSUPPORTED.  Grids whose rows TMA cannot describe run
  * one step per pass whatever the setting. */
 spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);

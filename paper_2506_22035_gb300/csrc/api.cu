@@ -114,7 +114,7 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
 int max_steps_per_pass(const spider_plan_t* p) {
-  if (p->wide()) return 1;
+  if (p->wide()) return p->ndim == 1 ? 4 : 1;
   if (p->ndim == 2) return 4;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
   if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
@@ -142,6 +142,7 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
   auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
   if (T > 1 && !(p->nx % 4 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch))) T = 1;
+  if (T > 1 && p->ndim == 1 && p->nx % 8 != 0) T = 1;  // the 1-D fused kernel's TMA view
   const int64_t full = steps / T;
   const int rem = (int)(steps % T);
   const int64_t npasses = full + (rem ? 1 : 0);

@@ -15,4 +15,17 @@ cudaError_t launch_wide_sp_tf32(int cls, int r, const LaunchCtx& ctx) {
     default: return cudaErrorNotSupported;
   }
 }
+
+cudaError_t launch_wide1d_fused_sp_tf32(int r, int T, const LaunchCtx& ctx) {
+  switch (r) {
+    case 1: return launch_wide1d_fused_r<1>(T, ctx);
+    case 2: return launch_wide1d_fused_r<2>(T, ctx);
+    case 3: return launch_wide1d_fused_r<3>(T, ctx);
+    case 4: return launch_wide1d_fused_r<4>(T, ctx);
+    case 5: return launch_wide1d_fused_r<5>(T, ctx);
+    case 6: return launch_wide1d_fused_r<6>(T, ctx);
+    case 7: return launch_wide1d_fused_r<7>(T, ctx);
+    default: return cudaErrorNotSupported;
+  }
+}
 }  // namespace spider

@@ -76,6 +76,7 @@ namespace spider {
 cudaError_t launch_pass(const LaunchCtx& ctx, int T) {
   if (T <= 1) return launch_step(ctx);
   const spider_plan_t* p = ctx.plan;
+  if (p->ndim == 1) return p->wide() ? launch_wide1d_fused_sp_tf32(p->r, T, ctx) : cudaErrorNotSupported;
   if (p->ndim == 3) {
     if (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3)
       return launch_fused3d_sp_tf32(p->r, T, ctx);

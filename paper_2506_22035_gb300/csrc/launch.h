@@ -35,6 +35,9 @@ cudaError_t launch_dense_tf32(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_cuda_core(int cls, int r, const LaunchCtx& ctx);
 // Radius 4..7 (1-D and 2-D), sparse TF32, wide layout.
 cudaError_t launch_wide_sp_tf32(int cls, int r, const LaunchCtx& ctx);
+// Fused passes of T = 2..4 steps for 1-D sparse TF32 plans (wide layout,
+// lengths that are a multiple of 8).
+cudaError_t launch_wide1d_fused_sp_tf32(int r, int T, const LaunchCtx& ctx);
 
 // Fused passes of T = 2..4 time steps (2-D stencils, TMA-aligned grids).
 // cudaErrorNotSupported when no fused kernel applies; the caller then runs

@@ -489,6 +489,68 @@ cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
   return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
 
+// 1-D fused passes: tiles of 14 output rows of 128 points, every level on
+// 16 rows (8 warps x 2); needs the 8-float TMA view (length a multiple of 8).
+template <class C, bool RIN>
+cudaError_t launch_wide1d_fused_k(const LaunchCtx& ctx) {
+  const spider_plan_t* p = ctx.plan;
+  if (p->nx % 8 != 0) return cudaErrorNotSupported;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (!make_tensor_map(&map, ctx.src, 8, p->nx / 8, 1, 8, C::kBoxRows, 1)) return cudaErrorNotSupported;
+  auto kern = wide1d_fused_kernel<C, RIN>;
+  static std::mutex mu;
+  static int occ_by_dev[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (occ_by_dev[dev] == 0) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      int o = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      if (err != cudaSuccess) return err;
+      occ_by_dev[dev] = std::max(o, 1);
+    }
+    occ = occ_by_dev[dev];
+  }
+  StepArgs a;
+  a.src = ctx.src;
+  a.dst = ctx.dst;
+  a.nx = p->nx;
+  a.ny = 1;
+  a.nz = 1;
+  a.tiles_x = (int)((p->nx + C::NT - 1) / C::NT);
+  a.tiles_y = 1;
+  a.tiles_z = 1;
+  a.a_words = reinterpret_cast<const uint4*>(p->dev.a_words);
+  a.meta = p->dev.meta_words;
+  a.w = p->dev.w_dense;
+  a.status = p->dev.status;
+  a.use_tma = 1;
+  a.out_tf32 = ctx.out_tf32 ? 1 : 0;
+  const int grid = (int)std::min<long long>(a.tiles_x, (long long)occ * ctx.sms);
+  return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
+}
+
+template <int R>
+cudaError_t launch_wide1d_fused_r(int T, const LaunchCtx& ctx) {
+  auto go = [&](auto cfg) -> cudaError_t {
+    using C = decltype(cfg);
+    return ctx.in_tf32 ? launch_wide1d_fused_k<C, false>(ctx) : launch_wide1d_fused_k<C, true>(ctx);
+  };
+  switch (T) {
+    case 2: return go(Wide1DFusedCfg<R, 2, 14, 8>());
+    case 3: return go(Wide1DFusedCfg<R, 3, 14, 8>());
+    case 4: return go(Wide1DFusedCfg<R, 4, 14, 8>());
+    default: return cudaErrorNotSupported;
+  }
+}
+
 // 2-D: 8 warps x 8 rows x 128 columns, registers for 2 CTAs per SM; 1-D:
 // tiles of 16 rows of 128 points.
 template <int R>

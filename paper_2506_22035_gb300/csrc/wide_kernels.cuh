@@ -316,3 +316,154 @@ __global__ void __launch_bounds__(C::kThreads)
 }
 
 }  // namespace spider
+
+namespace spider {
+
+// 1-D temporal fusion: T steps per pass.  A tile of BY output rows of 128
+// points computes every level on BY + 2 rows -- its own plus one neighbour
+// row on each side -- so all level buffers share one layout: index
+// i <-> point X0 - 136 + i, 8 unused margin points at each end (always 0).
+// The windows of level t read level t-1 through the same 128-point row
+// trick as wide1d_kernel.  A level value depends on level t-1 within r
+// points only, so the garbage that enters from the margins creeps inward
+// r points per level and never reaches the BY output rows while
+// (T - 1) r <= 128.  Points outside the array are stored as 0 at every
+// level (the zero Dirichlet halo of every step) and intermediate levels are
+// stored rounded to TF32 as the next level's MMA reads them: bit-identical
+// to T single steps.  The input chunk is loaded by TMA (the 8-float view,
+// two boxes) into a ring of two stages.
+template <int RX_, int T_, int BY_, int NW_>
+struct Wide1DFusedCfg {
+  static constexpr int RZ = 0, RY = 0, RX = RX_, T = T_, NW = NW_;
+  static constexpr int kMinBlocks = 1;
+  static constexpr int BY = BY_;                  // output rows per tile
+  static constexpr int LR = BY + 2;               // rows of every level
+  static constexpr int H = LR / NW;               // level rows per warp
+  static constexpr int SX = 128;
+  static constexpr int NT = BY * SX;              // output points per tile
+  static constexpr int kOff = SX + kWideHalo;     // buffer index of point X0
+  static constexpr int kBuf = LR * SX + 2 * kWideHalo;  // floats of every level buffer
+  static constexpr int kBoxRows = ((kBuf / 8 + 1) / 2 + 3) / 4 * 4;  // two boxes, 128-byte aligned
+  static constexpr int kInBytes = 2 * kBoxRows * 8 * 4;
+  static constexpr int kInStride = (kInBytes + 1023) / 1024 * 1024;
+  static constexpr int kLvStride = (kBuf * 4 + 1023) / 1024 * 1024;
+  static constexpr int kThreads = NW * 32;
+  static constexpr int kSmemBytes = 2 * kInStride + 2 * kLvStride + 1024 + 64;
+  static constexpr int NKR = 1;
+  static_assert(LR % NW == 0 && H >= 1, "level rows split evenly over the warps");
+  static_assert((T - 1) * RX <= SX, "margin garbage must not reach the output rows");
+  static_assert(2 * kBoxRows * 8 >= kBuf && (kBoxRows * 32) % 128 == 0 && kBoxRows <= 256, "TMA boxes");
+  static_assert(T >= 2 && T <= 4, "steps per pass");
+};
+
+template <class C, bool RIN>
+__global__ void __launch_bounds__(C::kThreads)
+    wide1d_fused_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base_u32 = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
+  auto in_stage = [&](int s) { return reinterpret_cast<float*>(smem + s * C::kInStride); };
+  float* lv[2] = {reinterpret_cast<float*>(smem + 2 * C::kInStride),
+                  reinterpret_cast<float*>(smem + 2 * C::kInStride + C::kLvStride)};
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * C::kInStride + 2 * C::kLvStride);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int64_t n = args.nx;
+  const int ntiles = args.tiles_x;
+  auto issue = [&](int t, int s) {
+    // buffer index 0 is point X0 - 136, a multiple of 8
+    const int row8 = (int)(((int64_t)t * C::NT - C::kOff) / 8);
+    mbar_arrive_expect_tx(&full[s], C::kInBytes);
+    tma_load_3d(in_stage(s), &tmap, &full[s], 0, row8, 0);
+    tma_load_3d(in_stage(s) + C::kBoxRows * 8, &tmap, &full[s], 0, row8 + C::kBoxRows, 0);
+  };
+
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_mbar_init();
+  }
+  // level buffers: zero margins (never written afterwards)
+  for (int i = tid; i < C::kBuf; i += C::kThreads) lv[0][i] = lv[1][i] = 0.f;
+  griddep_wait();  // see stencil_step_kernel
+  griddep_launch_dependents();
+  __syncthreads();
+  if (tid == 0) {
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+  const int coff = 16 * g + phi_wide(0, q);
+
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    float* S = in_stage(s);
+    const int64_t x0 = (int64_t)t * C::NT;
+    const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+    if (!__syncthreads_and(ok)) break;
+    if (RIN) {
+      for (int i = tid; i < C::kBuf; i += C::kThreads) S[i] = __uint_as_float(cvt_tf32(S[i]));
+      __syncthreads();
+    }
+    // this warp's level rows warp*H .. warp*H+H-1; level row i covers points
+    // x0 - 128 + 128 i .. +127 and reads the buffer from index 128 i
+    const int64_t xw = x0 - C::SX + (int64_t)(warp * C::H) * C::SX + 32 * q + g;
+    const int offs[4] = {0, 16, 8, 24};
+#pragma unroll 1
+    for (int level = 1; level <= C::T; ++level) {
+      const float* src = level == 1 ? S : lv[(level - 2) & 1];
+      float acc[C::H][4];
+#pragma unroll
+      for (int i = 0; i < C::H; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      wide_groups<C, 0>(smem_u32(src + (warp * C::H) * C::SX + coff), args, lane, acc);
+      if (level < C::T) {
+        float* d = lv[(level - 1) & 1] + kWideHalo + (warp * C::H) * C::SX + 32 * q + g;
+#pragma unroll
+        for (int yy = 0; yy < C::H; ++yy)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int64_t x = xw + yy * C::SX + offs[j];
+            d[yy * C::SX + offs[j]] = (x >= 0 && x < n) ? __uint_as_float(cvt_tf32(acc[yy][j])) : 0.f;
+          }
+      } else {
+        if (args.out_tf32) {
+#pragma unroll
+          for (int i = 0; i < C::H; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = __uint_as_float(cvt_tf32(acc[i][j]));
+        }
+#pragma unroll
+        for (int yy = 0; yy < C::H; ++yy) {
+          const int row = warp * C::H + yy;  // output rows are level rows 1 .. BY
+          if (row < 1 || row > C::BY) continue;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int64_t x = xw + yy * C::SX + offs[j];
+            if (x < n) args.dst[x] = acc[yy][j];
+          }
+        }
+      }
+      __syncthreads();  // level complete before the next one reads it
+      if (level == 1 && tid == 0) {
+        // the input stage is no longer read: load the tile two ahead into it
+        const int tn = t + 2 * (int)gridDim.x;
+        if (tn < ntiles) {
+          fence_proxy_async_smem();
+          issue(tn, s);
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int t = blockIdx.x + (it + k) * gridDim.x;
+      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+    }
+  }
+}
+
+}  // namespace spider

@@ -291,11 +291,13 @@ def test_domain_argument_validation(lib):
 
 
 def test_steps_per_pass_where_fusion_is_built(lib):
-    # fused passes exist for 2-D stencils and for 3-D radius-1 sparse TF32 plans
+    # fused passes exist for 2-D stencils of radius 1..3, and for 3-D radius-1
+    # and 1-D sparse TF32 plans
     def plan(nd, r, prec="tf32"):
         return spider.Plan(np.full((2 * r + 1,) * nd, 0.1, np.float32), (16,) * nd, "box", prec)
     for nd, r, prec, ok in ((2, 3, "tf32", True), (2, 1, "f16x2", True), (3, 1, "tf32", True),
-                            (3, 2, "tf32", False), (3, 1, "f16x2", False), (1, 1, "tf32", False)):
+                            (3, 2, "tf32", False), (3, 1, "f16x2", False), (1, 1, "tf32", True),
+                            (1, 7, "tf32", True), (1, 2, "f16x2", False), (2, 5, "tf32", False)):
         p = plan(nd, r, prec)
         for T in (2, 4):
             if ok:
@@ -398,8 +400,11 @@ def test_wide_radius_limits(lib):
         with pytest.raises(spider.SpiderError) as e:
             p.set_engine("dense_tc")
         assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
-        with pytest.raises(spider.SpiderError):
-            p.set_steps_per_pass(2)
+        if nd == 1:
+            p.set_steps_per_pass(4)  # 1-D wide plans have fused passes
+        else:
+            with pytest.raises(spider.SpiderError):
+                p.set_steps_per_pass(2)
         p.close()
     for nd, r, prec in ((3, 4, "tf32"), (2, 8, "tf32"), (2, 5, "f16x2"), (1, 4, "bf16x3")):
         with pytest.raises(spider.SpiderError) as e:

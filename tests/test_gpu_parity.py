@@ -216,14 +216,19 @@ def test_constant_field_invariant_on_gpu(prec):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "f16x2", "bf16x3"])
-def test_box2d_r3_8192_full_size_sampled(prec):
-    # the benchmark workload at full size and full step count; the oracle
-    # evaluates sampled points exactly through their dependency cones
+@pytest.mark.parametrize("tuned", [False, True])
+def test_box2d_r3_8192_full_size_sampled(prec, tuned):
+    # the benchmark workload at full size and full step count, one step per
+    # pass and in the configuration the autotuner picks (the one bench.py
+    # times); the oracle evaluates sampled points exactly through their
+    # dependency cones
     wl = si.BOX2D_R3_8192
     u0, w = si.workload_inputs(wl)
     plan = spider.Plan(w, u0.shape, "box", prec)
     a = torch.from_numpy(u0).cuda()
     b = torch.empty_like(a)
+    if tuned:
+        plan.autotune(a, b, wl.steps)
     plan.run(a, b, wl.steps)
     plan.sync()
     n = u0.shape[0]
@@ -233,6 +238,28 @@ def test_box2d_r3_8192_full_size_sampled(prec):
     rms = np.sqrt(spider.norms_fp64(b)[0] / b.numel())
     tol = {"tf32": 2e-2, "f16x2": 1e-4, "bf16x3": 1e-3}[prec]
     assert np.all(np.abs(got - ref) <= tol * rms), (got, ref, rms)
+    plan.close()
+
+
+@pytest.mark.parametrize("wl", [si.HEAT3D_512, si.BOX3D_512], ids=["heat3d", "box3d"])
+def test_3d_512_full_size_sampled(wl):
+    # the 3-D benchmark workloads at full size and step count, autotuned as
+    # bench.py runs them; sampled points (corners, edges, faces, interior)
+    # from the oracle's exact dependency-cone evaluation
+    u0, w = si.workload_inputs(wl)
+    plan = spider.Plan(w, u0.shape, wl.shape, "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    plan.autotune(a, b, wl.steps)
+    plan.run(a, b, wl.steps)
+    plan.sync()
+    n = u0.shape[0]
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n // 2, n - 1), (n // 2, n // 2, n // 2), (100, 400, 3),
+           (n - 1, 0, 255)]
+    ref = oracle.stencil_points(u0, w, wl.steps, pts)
+    got = b[tuple(np.array(pts).T)].cpu().numpy().astype(np.float64)
+    rms = np.sqrt(spider.norms_fp64(b)[0] / b.numel())
+    assert np.all(np.abs(got - ref) <= 2e-2 * rms), (got, ref, rms)
     plan.close()
 
 
@@ -348,6 +375,24 @@ def test_wide_radius_parity_and_chained_calls(r, shape):
         star_w = si.normalised_coeffs(2, r, "star", g)
         check_close(gpu_run(u0, star_w, 4, "star", "tf32", "sparse_tc"), oracle.stencil(u0, star_w, 4),
                     ("sparse_tc", "tf32"))
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, 7])
+@pytest.mark.parametrize("n", [10240, 3000, 1792, 96, 2052])
+def test_fused_1d_passes_match_single_steps(r, n):
+    # 1-D passes compute every level on the tile's rows plus one neighbour row
+    # each side; margins never reach the output rows and points outside the
+    # array are zero at every level: bit-identical to single steps.  1792 is
+    # one tile, 96 less than a row, 2052 not a multiple of 8 (one step per
+    # pass, the fused kernel's TMA view needs multiples of 8).
+    g = si.rng(19, r)
+    u0 = si.grid((n,), -1, 1, g)
+    w = si.normalised_coeffs(1, r, "box", g)
+    single = gpu_run(u0, w, 9, "box", "tf32", "sparse_tc", 1)
+    for T in (2, 3, 4):
+        fused = gpu_run(u0, w, 9, "box", "tf32", "sparse_tc", T)
+        assert np.array_equal(fused, single), (r, n, T)
+    check_close(single, oracle.stencil(u0, w, 9), ("sparse_tc", "tf32"))
 
 
 @pytest.mark.parametrize("T", [2, 3, 4])
