@@ -45,8 +45,8 @@ static void free_device(spider_plan_t* p) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != d.device) cudaSetDevice(d.device);
-    drop_graphs(p);
-    if (d.capture_stream) cudaStreamDestroy(d.capture_stream);
+    // cudaFree waits for the device, so no replay of a cached graph is still
+    // running when the graphs are destroyed
     cudaFree(d.a_words);
     cudaFree(d.meta_words);
     cudaFree(d.w_dense);
@@ -54,6 +54,8 @@ static void free_device(spider_plan_t* p) {
     cudaFree(d.host_stage_in);
     cudaFree(d.host_stage_out);
     cudaFree(d.status);
+    drop_graphs(p);
+    if (d.capture_stream) cudaStreamDestroy(d.capture_stream);
     if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
   }
   d = DeviceState();
@@ -322,11 +324,11 @@ spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
   // drop device copies of the old operands (uploaded again lazily) and the
   // run graphs that read them
   if (p->dev.device >= 0) {
-    drop_graphs(p);
-    cudaFree(p->dev.a_words);
+    cudaFree(p->dev.a_words);  // waits for the device: no graph replay is running
     cudaFree(p->dev.meta_words);
     p->dev.a_words = nullptr;
     p->dev.meta_words = nullptr;
+    drop_graphs(p);
   }
   return SPIDER_OK;
 }
