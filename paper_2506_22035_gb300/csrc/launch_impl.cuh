@@ -91,6 +91,28 @@ cudaError_t launch_cfg(const LaunchCtx& ctx) {
   return launch_cfg_k<C, MODE, true, STAR>(ctx);
 }
 
+// Number of z chunks per column block for the z-streaming kernels.  Items
+// (column, chunk) of equal length run in waves of `slots` resident CTAs; a
+// chunk of c planes costs c + `halo` plane times (its halo planes are read,
+// or recomputed, twice).  The count minimises waves x (nz / chunks + halo)
+// over chunks of at least `min_planes` planes: one wave of long chunks when
+// the columns fill the slots evenly, more waves of shorter chunks when one
+// wave would leave many slots idle.
+inline long long choose_z_chunks(long long ncol, long long slots, long long nz, long long halo, long long min_planes) {
+  const long long max_chunks = std::max<long long>(1, nz / min_planes);
+  long long best = 1;
+  double best_cost = 1e300;
+  for (long long c = 1; c <= max_chunks; ++c) {
+    const long long waves = (ncol * c + slots - 1) / slots;
+    const double cost = (double)waves * ((double)nz / (double)c + (double)halo);
+    if (cost < best_cost * (1.0 - 1e-9)) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
 // 3-D z-streaming launch (TMA-describable grids); cudaErrorNotSupported
 // otherwise, and the caller uses the cube-tiled kernel.
 template <class C, Mode MODE, bool RIN, bool STAR>
@@ -136,9 +158,10 @@ cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ncol = (long long)a.tiles_x * a.tiles_y;
   const long long slots = (long long)occ * ctx.sms;
-  // z chunks: enough items for four per resident CTA, chunks of >= 8 planes
-  long long nchunks = std::max<long long>(1, (4 * slots + ncol - 1) / ncol);
-  nchunks = std::min<long long>(nchunks, std::max<long long>(1, p->nz / 8));
+  // z chunks of >= 8 planes, 2r halo planes each (on 512^3 TF32 this is one
+  // wave of 73-plane chunks; four short chunks per CTA re-read 11 % of the
+  // planes)
+  const long long nchunks = choose_z_chunks(ncol, slots, p->nz, 2 * C::RZ, 8);
   if (ncol * nchunks > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ncol * nchunks, slots);
   cudaLaunchConfig_t cfg = {};
@@ -341,10 +364,9 @@ cudaError_t launch_fused3d_k(const LaunchCtx& ctx) {
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ncol = (long long)a.tiles_x * a.tiles_y;
   const long long slots = (long long)occ * ctx.sms;
-  // z chunks: about four items per resident CTA, chunks of >= 32 planes (each
-  // chunk recomputes 2r(T-t) planes of level t at its ends)
-  long long nchunks = std::max<long long>(1, (4 * slots + ncol - 1) / ncol);
-  nchunks = std::min<long long>(nchunks, std::max<long long>(1, p->nz / 32));
+  // z chunks of >= 32 planes; a chunk reads 2rT extra input planes and
+  // recomputes 2r(T-t) planes of level t at its ends
+  const long long nchunks = choose_z_chunks(ncol, slots, p->nz, 2 * F::R * F::T, 32);
   if (ncol * nchunks > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ncol * nchunks, slots);
   cudaLaunchConfig_t cfg = {};
