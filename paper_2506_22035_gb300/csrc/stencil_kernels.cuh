@@ -47,7 +47,7 @@ struct StepArgs {
   int out_tf32;            // TF32 modes: store the outputs rounded to TF32 (the grid feeds another step)
 };
 
-// TF32 modes round every B operand to TF32 (round to nearest, ties away)
+// TF32 modes round every B operand to TF32 (round to nearest, ties to even)
 // before the MMA.  A grid written for another step of the same run can hold
 // its values already rounded that way: the reading step then passes the raw
 // bits to the MMA (kernel template flag RIN = false) and gets bit-identical
