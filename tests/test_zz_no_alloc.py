@@ -64,3 +64,22 @@ def test_static_entry_point_matches_spider_run_on_two_calls_in_a_row():
         assert torch.isfinite(got).all()
         assert _rel(got, ref) <= tol
         plan.close()
+
+
+@pytest.mark.parametrize("shape,r", [((130, 300), 5), ((5000,), 2)])
+def test_static_entry_point_runs_the_wide_layout(shape, r):
+    # radius 4..7 and 1-D plans run the wide layout through the same arrays
+    native = _lib()
+    import paper_2506_22035_gb300 as spider
+    g = si.rng(40, r)
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(len(shape), r, "box", g)
+    plan = spider.Plan(w, shape, "box", "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b_static, b_run = torch.empty_like(a), torch.empty_like(a)
+    _run(native, "spider_run_static", plan, a, b_static, 5)
+    plan.run(a, b_run, 5)
+    plan.sync()
+    torch.cuda.synchronize()
+    assert torch.equal(b_static, b_run)
+    plan.close()
