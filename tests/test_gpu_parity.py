@@ -430,13 +430,15 @@ def test_autotune_keeps_results_within_tolerance():
 def _batch_jobs():
     jobs = []
     g = np.random.default_rng(77)
-    shapes = [(300, 520), (64, 128), (1, 512), (257, 1000), (90, 132), (70, 130), (128, 256), (33, 64)]
+    # the last two grids have >= 2^21 points (many tiles per step in the queue)
+    shapes = [(300, 520), (64, 128), (1, 512), (257, 1000), (90, 132), (70, 130), (128, 256), (33, 64),
+              (1500, 1500), (1100, 2000)]
     for i, ext in enumerate(shapes):
         r = 1 + i % 3
         kind = "box" if i % 2 == 0 else "star"
         u0 = g.uniform(0, 1, ext).astype(np.float32)
         w = si.normalised_coeffs(2, r, kind, g)
-        steps = [1, 7, 12, 3, 20, 2, 9, 5][i]
+        steps = [1, 7, 12, 3, 20, 2, 9, 5, 7, 4][i]
         jobs.append((u0, w, kind, steps))
     return jobs
 
@@ -456,6 +458,11 @@ def test_batch_persistent_queue_matches_individual_runs():
         got = outs[k].cpu().numpy()
         assert np.array_equal(got, refs[k]), k               # same tile arithmetic, bit for bit
         assert np.array_equal(ins[k].cpu().numpy(), u0)
+    # the plans are unchanged by the batch
+    outs[-1].fill_(float("nan"))
+    plans[-1].run(ins[-1], outs[-1], jobs[-1][3])
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[-1].cpu().numpy(), refs[-1])
     # and against the oracle for one job
     u0, w, kind, steps = jobs[3]
     check_close(outs[3].cpu().numpy(), oracle.stencil(u0, w, steps), ("sparse_tc", "tf32"))
