@@ -113,10 +113,12 @@ spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pas
 /* Tile shape of the fused kernels.  2-D: 0 = warp units of 8 output rows and
  * two input boxes in flight; 1 = 16 rows (more independent MMAs per warp), two
  * boxes; 2 = 8 rows, one box, registers capped so three CTAs share an SM;
- * 3 = 16 rows, one box.  3-D: 0 = column blocks of 16 level-1 rows, warp
- * units of 4 rows; 1 and 3 = 32 rows, units of 8; 2 = as 0 with registers
- * capped for three CTAs per SM at 2 steps per pass.  Any other value returns
- * SPIDER_ERR_INVALID.  spider_plan_autotune sets it. */
+ * 3 = 16 rows, one box; 4 = small tiles (level 1 of 32 rows instead of 64,
+ * one warp unit per warp per level) for grids that do not fill the GPU.
+ * 3-D: 0 and 4 = column blocks of 16 level-1 rows, warp units of 4 rows; 1
+ * and 3 = 32 rows, units of 8; 2 = as 0 with registers capped for three CTAs
+ * per SM at 2 steps per pass.  Any other value returns SPIDER_ERR_INVALID.
+ * spider_plan_autotune sets it. */
 spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 
 /* spider_plan_autotune -- measures the plan's configurations on the caller's

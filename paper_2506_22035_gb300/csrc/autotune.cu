@@ -28,7 +28,7 @@ using namespace spider;
 
 extern "C" spider_status spider_plan_set_tile_variant(spider_plan p, int variant) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
-  if (variant < 0 || variant > 3) return fail(SPIDER_ERR_INVALID, "tile variant must be 0..3");
+  if (variant < 0 || variant > 4) return fail(SPIDER_ERR_INVALID, "tile variant must be 0..4");
   std::lock_guard<std::mutex> lock(p->mu);
   p->tile_variant = variant;
   return SPIDER_OK;
@@ -65,7 +65,11 @@ extern "C" spider_status spider_plan_autotune(spider_plan p, const float* grid_i
   int best_T = 1, best_v = 0;
   spider_status st = SPIDER_OK;
   for (int T = 1; T <= maxT && st == SPIDER_OK; ++T) {
-    for (int v = 0; v < (T > 1 ? 4 : 1) && st == SPIDER_OK; ++v) {
+    // variant 4 (small 2-D tiles) only where the grid cannot fill the GPU
+    // with the 64-row tiles
+    const bool small2d = p->ndim == 2 && p->points() <= (int64_t(1) << 22);
+    const int nv = T == 1 ? 1 : small2d ? 5 : 4;
+    for (int v = 0; v < nv && st == SPIDER_OK; ++v) {
       p->steps_per_pass = T;
       p->tile_variant = v;
       st = run_device(p, grid_in, grid_out, steps, stream);  // warm-up

@@ -281,25 +281,29 @@ cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
 //   0: H = 8,  two input boxes in flight      1: H = 16, two input boxes
 //   2: H = 8,  one input box, registers capped for 3 CTAs per SM
 //   3: H = 16, one input box
-template <int R, int T, int H, int MINB, int INS>
-using FusedTile = FuseCfg<R, T, 64 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB, INS>;
+template <int R, int T, int H, int MINB, int INS, int L1 = 64>
+using FusedTile = FuseCfg<R, T, L1 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB, INS>;
 
-template <Mode MODE, int R, int H, int MINB, int INS>
+template <Mode MODE, int R, int H, int MINB, int INS, int L1 = 64>
 cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
   switch (T) {
-    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB, INS>, MODE>(ctx);
-    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB, INS>, MODE>(ctx);
-    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB, INS>, MODE>(ctx);
+    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB, INS, L1>, MODE>(ctx);
+    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB, INS, L1>, MODE>(ctx);
+    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB, INS, L1>, MODE>(ctx);
     default: return cudaErrorNotSupported;
   }
 }
 
 // Variants 2 and 3 exist for the TF32 sparse mode only (the split and dense
 // modes need more registers than variant 2 allows); elsewhere they run as
-// variants 0 and 1.
+// variants 0 and 1.  Variant 4 is the small tile: level 1 of 32 rows, one
+// warp unit per warp per level, four times the tiles of the 64-row shapes --
+// for grids too small to fill the GPU, where a pass is the latency of one
+// tile's levels.
 template <Mode MODE, int R>
 cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
   int v = ctx.plan->tile_variant;
+  if (v == 4) return launch_fused_rh<MODE, R, 8, 1, 2, 32>(T, ctx);
   if (MODE != Mode::SpTF32 && v >= 2) v -= 2;
   if constexpr (MODE == Mode::SpTF32) {
     if (v == 2) return launch_fused_rh<MODE, R, 8, 3, 1>(T, ctx);
@@ -396,6 +400,7 @@ cudaError_t launch_fused3d_cfg(const LaunchCtx& ctx) {
 //              per SM (1 for T = 4, whose rings need 114 KB)
 //   variant 1, 3: L1Y = 32, warp units of 8 rows, 8 warps, one CTA per SM
 //   variant 2: as 0 with registers capped for 3 CTAs per SM at T = 2
+//   variant 4: as 0
 template <Mode MODE, int T>
 cudaError_t launch_fused3d_t(const LaunchCtx& ctx) {
   constexpr int kMinB = T == 4 ? 1 : 2;

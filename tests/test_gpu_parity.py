@@ -279,7 +279,7 @@ def test_fused_passes_match_single_steps(key, r):
     single = gpu_run(u0, w, 7, "box", key[1], key[0], 1)
     ref = oracle.stencil(u0, w, 7)
     exact = key[1] == "tf32" or r % 2 == 0
-    for T, variant in ((2, 0), (3, 1), (4, 2), (2, 1), (2, 2), (4, 1), (2, 3), (3, 3)):
+    for T, variant in ((2, 0), (3, 1), (4, 2), (2, 1), (2, 2), (4, 1), (2, 3), (3, 3), (2, 4), (4, 4)):
         fused = gpu_run(u0, w, 7, "box", key[1], key[0], T, variant)
         if exact:
             assert np.array_equal(fused, single), (key, r, T)
