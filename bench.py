@@ -205,9 +205,38 @@ def cpu_baseline(wl, budget_s: float = 12.0):
     oracle.stencil(u0, w, steps)
     dt = time.perf_counter() - t0
     pts = int(np.prod(u0.shape))
+    # one core, on a crop of the grid (a bounded sample, about a second)
+    side = [min(n, 1024) for n in u0.shape] if u0.ndim < 3 else [min(n, 128) for n in u0.shape]
+    crop = np.ascontiguousarray(u0[tuple(slice(0, n) for n in side)])
+    t1 = time.perf_counter()
+    oracle.stencil(crop, w, 1, threads=1)
+    dt1 = max(time.perf_counter() - t1, 1e-6)
     return {"value": pts * steps / dt / 1e9, "unit": "GStencil/s", "cores": cores, "kind": "oracle",
+            "cpu": host_cpu_model(),
+            "value_1core": crop.size / dt1 / 1e9,
             "sample": f"{wl.name} grid {'x'.join(map(str, u0.shape))}, {steps} of its {wl.steps} time steps, "
-                      f"FP64 direct stencil (C, OpenMP, {cores} threads), {dt:.1f} s"}
+                      f"FP64 direct stencil (C, OpenMP, {cores} threads), {dt:.1f} s; 1 core: one step of a "
+                      f"{'x'.join(map(str, crop.shape))} crop"}
+
+
+def host_cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo, or lscpu's fields on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------ reference arm
