@@ -51,6 +51,7 @@ static void free_device(spider_plan_t* p) {
     cudaFree(d.meta_words);
     cudaFree(d.w_dense);
     cudaFree(d.scratch);
+    cudaFree(d.pad);
     cudaFree(d.host_stage_in);
     cudaFree(d.host_stage_out);
     cudaFree(d.status);
@@ -99,6 +100,20 @@ static spider_status ensure_scratch(spider_plan_t* p) {
     return fail(SPIDER_ERR_OOM, std::string("scratch grid: ") + cudaGetErrorString(e));
   }
   p->dev.scratch_bytes = bytes;
+  return SPIDER_OK;
+}
+
+spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes) {
+  if (p->dev.pad && p->dev.pad_bytes >= bytes) return SPIDER_OK;
+  cudaFree(p->dev.pad);  // waits for the device: no earlier batch still uses it
+  p->dev.pad = nullptr;
+  p->dev.pad_bytes = 0;
+  cudaError_t e = cudaMalloc(&p->dev.pad, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPIDER_ERR_OOM, std::string("padded grids: ") + cudaGetErrorString(e));
+  }
+  p->dev.pad_bytes = bytes;
   return SPIDER_OK;
 }
 

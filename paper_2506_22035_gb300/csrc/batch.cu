@@ -34,19 +34,30 @@ constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
 constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
 constexpr int kMaxTableSmem = 48 * 1024;
 
+// Step s reads `in` (s = 0) or bufs[(first + s - 1) % 2] and writes `out`
+// (the last step) or bufs[(first + s) % 2].  When in, out and the plan's
+// scratch grid are all TMA-describable, bufs = {out, scratch} with the parity
+// `first` chosen so that the last step lands in out, and pitch = nx.
+// Otherwise (rows of nx floats are not a multiple of 16 bytes, or a buffer is
+// not 16-byte aligned) bufs are the plan's two padded grids with rows `pitch`
+// (nx rounded up to 4) floats apart, first = 0: every step but the first then
+// loads through TMA, and only the first step's halo boxes are loaded by the
+// consumers (`tma0` = 0).
 struct BatchJob {
   int64_t nx, ny;
+  int64_t pitch;       // row pitch of bufs (floats)
   int r;
   int tiles_x, tiles_y;
   int steps;
-  int first;           // parity of the first destination (last step lands in out)
-  int map0;            // tensor maps: map0 + 0 = in, + 1 = out, + 2 = scratch
+  int first;
+  int map0;            // tensor maps: map0 + 0 = in, + 1 = bufs[0], + 2 = bufs[1]
   const uint4* a;      // packed A operands (TF32, per A index)
   const uint32_t* meta;
-  float* bufs[2];      // out, scratch
+  float* bufs[2];
+  float* out;
   const float* in;
   int* done;           // per-tile count of completed steps
-  int tma;             // 1: rows and buffers TMA-describable; 0: consumers load the halo box
+  int tma0;            // 1: `in` is TMA-describable; 0: consumers load the first step's boxes
 };
 
 template <int R>
@@ -61,9 +72,16 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One tile of one step: operands to registers, MMAs, write-back.
-template <int R>
-__device__ __forceinline__ void batch_tile(const BatchJob& jb, const float* S, float* dst, int x0, int y0) {
+// One tile of one step: operands to registers, MMAs, write-back.  Every step
+// but a job's last stores its outputs rounded to TF32 (`out_tf32`), so the
+// steps after the first read operands that need no rounding (RIN = false);
+// the MMA sees the same values either way.
+// A8 / E8 hold the job's packed operands (the first 2R + 2 entries).
+constexpr int kNA = 2 * kMaxR + 2;
+template <int R, bool RIN>
+__device__ __forceinline__ void batch_tile(const BatchJob& jb, const uint4 (&A8)[kNA], const uint32_t (&E8)[kNA],
+                                           const float* S, float* dst, int64_t pitch, int x0, int y0,
+                                           bool out_tf32) {
   using C = BatchTile<R>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, q = lane & 3;
@@ -72,8 +90,8 @@ __device__ __forceinline__ void batch_tile(const BatchJob& jb, const float* S, f
   uint32_t E[C::NA];
 #pragma unroll
   for (int a = 0; a < C::NA; ++a) {
-    A[a] = jb.a[(size_t)a * 32 + lane];
-    E[a] = jb.meta[(size_t)a * 32 + lane];
+    A[a] = A8[a];
+    E[a] = E8[a];
   }
   float acc[C::H / 2][4];
 #pragma unroll
@@ -81,9 +99,10 @@ __device__ __forceinline__ void batch_tile(const BatchJob& jb, const float* S, f
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
   const float* row0 = S + (size_t)(wy * C::H) * C::SX + wx * 64 + 8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
-  plane_sp_tf32<C>(row0, A, E, acc);
+  plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
+  if (out_tf32) round_tf32_inplace(acc);
   const int ybase = y0 + wy * C::H, xbase = x0 + wx * 64;
-  float* o = dst + (int64_t)ybase * jb.nx + xbase + 16 * q + g;
+  float* o = dst + (int64_t)ybase * pitch + xbase + 16 * q + g;
   const int ylim = (int)(jb.ny - ybase < C::H ? jb.ny - ybase : C::H);
   const int xlim = (int)(jb.nx - xbase < 64 ? jb.nx - xbase : 64);
 #pragma unroll
@@ -93,7 +112,7 @@ __device__ __forceinline__ void batch_tile(const BatchJob& jb, const float* S, f
       if (2 * pp + sr < ylim) {
 #pragma unroll
         for (int c = 0; c < 2; ++c)
-          if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * jb.nx + 8 * c] = acc[pp][2 * sr + c];
+          if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * pitch + 8 * c] = acc[pp][2 * sr + c];
       }
 }
 
@@ -117,15 +136,35 @@ struct ItemSlot {
   int job, s, tile, end;
 };
 
-// kThreads consumer threads (8 warps) compute tiles; one extra producer warp
-// claims items, waits for their dependencies and issues their TMA loads into
-// a two-stage ring, so the queue latency overlaps the tensor-core work.
+// Waits for phase `parity` of `bar` like mbar_wait_bounded, but sleeps
+// `ns` nanoseconds between polls, so a warp that waits for a long time (a
+// producer two items ahead of its consumers) leaves the issue slots to the
+// warps that compute.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, int* status, unsigned ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(status, kStatusTimeout);
+      return false;
+    }
+    __nanosleep(ns);
+  }
+  return true;
+}
+
+// kThreads consumer threads (8 warps) compute tiles; two producer warps, one
+// per stage of a two-stage ring, claim items, wait for their dependencies and
+// issue their TMA loads, so the queue latency of two items overlaps the
+// tensor-core work.  Claims stay in the order the consumers process the
+// stages (a shared turn counter), so every CTA processes its items in claim
+// order, which keeps the queue free of deadlock (see above).
 // The queue tables (job records, job order, step offsets, jobs active per
 // step, tile prefix sums) are one contiguous block `tables` of `tables_bytes`
 // bytes whose parts start at the given offsets.  When `tables_in_smem` is set
 // the CTA copies the block into shared memory first, so claiming and decoding
 // an item costs one global atomic and no other global round trip.
-__global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned char* __restrict__ tables,
+__global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned char* __restrict__ tables,
                                                              int tables_bytes, int tables_in_smem, int o_order,
                                                              int o_step, int o_active, int o_tp,
                                                              const CUtensorMap* __restrict__ maps, int max_steps,
@@ -136,6 +175,7 @@ __global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned cha
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kStageStride);
   uint64_t* empty = full + 2;
   ItemSlot* slot = reinterpret_cast<ItemSlot*>(empty + 2);
+  volatile long long* claim_turn = reinterpret_cast<volatile long long*>(slot + 2);
   unsigned char* tsm = smem + 2 * kStageStride + 128;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tables_in_smem) {
@@ -152,42 +192,69 @@ __global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned cha
   if (tid == 0) {
     for (int k = 0; k < 2; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], 1);
+      mbar_init(&empty[k], kThreads / 32);  // one arrival per consumer warp
     }
+    *claim_turn = 0;
     fence_mbar_init();
   }
   __syncthreads();
   const long long total = step_off[max_steps];
 
-  if (warp == kThreads / 32) {
-    // ---------------- producer warp ----------------
-    for (long long k = 0;; ++k) {
-      const int st = (int)(k & 1);
-      const long long use = k >> 1;
+  if (warp >= kThreads / 32) {
+    // ---------------- producer warps: warp p owns stage p ----------------
+    const int st = warp - kThreads / 32;
+    int pj = -1, ptile = 0, ps = 0;  // the item this stage held last
+    for (long long use = 0;; ++use) {
+      const long long k = 2 * use + st;  // the consumers' index of this item
+      // claim in the consumers' order: item k only after item k - 1.  The
+      // claim and the decode run while the stage still holds item k - 2.
       long long item = 0;
-      if (lane == 0) item = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ULL);
-      item = __shfl_sync(0xffffffffu, item, 0);
-      // the stage must have been released by the consumers (use - 1)
-      if (use > 0) {
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), status);
-        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+      bool ok = true;
+      if (lane == 0) {
+        const long long t0 = clock64();
+        while (*claim_turn != k) {
+          if (clock64() - t0 > kWaitCycles) { atomicExch(status, kStatusTimeout); ok = false; break; }
+          __nanosleep(64);
+        }
+        if (ok) {
+          __threadfence_block();  // the other warp's claim before this one
+          item = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ULL);
+          __threadfence_block();
+          *claim_turn = k + 1;
+        }
       }
-      if (item >= total) {
+      if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+      item = __shfl_sync(0xffffffffu, item, 0);
+      const bool end = item >= total;
+      int s = 0, j = 0, tile = 0, tx = 0, ty = 0;
+      if (!end) {
+        s = warp_search(step_off, max_steps, item, lane);
+        const long long local = item - step_off[s];
+        const int kk = warp_search(tile_prefix, active[s], local, lane);
+        j = order[kk];
+        tile = (int)(local - tile_prefix[kk]);
+        tx = tile % jobs[j].tiles_x;
+        ty = tile / jobs[j].tiles_x;
+      }
+      // every consumer warp must have handed the stage back (use - 1); its
+      // stores of that item are then ordered before this warp's release of
+      // the item's step counter (the fence waits here, not in the consumers)
+      if (use > 0) {
+        if (lane == 0) ok = mbar_wait_backoff(&empty[st], (uint32_t)((use - 1) & 1), status, 128);
+        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+        if (lane == 0 && pj >= 0) st_release(jobs[pj].done + ptile, ps + 1);
+      }
+      if (end) {
         if (lane == 0) {
           slot[st].end = 1;
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         }
         break;
       }
-      const int s = warp_search(step_off, max_steps, item, lane);
-      const long long local = item - step_off[s];
-      const int kk = warp_search(tile_prefix, active[s], local, lane);
-      const int j = order[kk];
       const BatchJob& jb = jobs[j];
-      const int tile = (int)(local - tile_prefix[kk]);
-      const int tx = tile % jb.tiles_x, ty = tile / jb.tiles_x;
-      // lanes 0..8 each wait for one tile of the 3 x 3 neighbourhood (step s-1)
+      // lanes 0..8 each wait for one tile of the 3 x 3 neighbourhood (step
+      // s-1); after the release above, so a wait on this CTA's own item k - 2
+      // cannot block its publication
       if (s > 0 && lane < 9) {
         const int ntx = tx + lane % 3 - 1, nty = ty + lane / 3 - 1;
         if (ntx >= 0 && nty >= 0 && ntx < jb.tiles_x && nty < jb.tiles_y) {
@@ -196,17 +263,21 @@ __global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned cha
             const long long t0 = clock64();
             while (ld_acquire(flag) < s) {
               if (clock64() - t0 > kWaitCycles) { atomicExch(status, kStatusTimeout); break; }
+              __nanosleep(128);
             }
           }
         }
       }
+      pj = j;
+      ptile = tile;
+      ps = s;
       __syncwarp();
       if (lane == 0) {
         slot[st].job = j;
         slot[st].s = s;
         slot[st].tile = tile;
         slot[st].end = 0;
-        if (jb.tma) {
+        if (s > 0 || jb.tma0) {
           // the neighbours' generic-proxy stores must be visible to the TMA read
           asm volatile("fence.proxy.async.global;" ::: "memory");
           const int src_map = jb.map0 + (s == 0 ? 0 : 1 + (jb.first + s - 1) % 2);
@@ -223,36 +294,57 @@ __global__ void __launch_bounds__(kThreads + 32) batch_kernel(const unsigned cha
   }
 
   // ---------------- consumer warps ----------------
+  // The packed operands of the current job stay in registers while its
+  // tiles follow one another.
+  uint4 A8[kNA];
+  uint32_t E8[kNA];
+  int cur_job = -1;
   for (long long k = 0;; ++k) {
     const int st = (int)(k & 1);
-    const bool landed = mbar_wait_bounded(&full[st], (uint32_t)((k >> 1) & 1), status);
+    const bool landed = mbar_wait_backoff(&full[st], (uint32_t)((k >> 1) & 1), status, 32);
     if (!landed) break;
     const ItemSlot it = slot[st];
     if (it.end) break;
     const BatchJob& jb = jobs[it.job];
+    if (it.job != cur_job) {
+      const int na = 2 * jb.r + 2;
+#pragma unroll
+      for (int a = 0; a < kNA; ++a)
+        if (a < na) {
+          A8[a] = jb.a[(size_t)a * 32 + lane];
+          E8[a] = jb.meta[(size_t)a * 32 + lane];
+        }
+      cur_job = it.job;
+    }
     const int tx = it.tile % jb.tiles_x, ty = it.tile / jb.tiles_x;
     float* Sw = reinterpret_cast<float*>(smem + st * kStageStride);
-    if (!jb.tma) {
-      const float* src = it.s == 0 ? jb.in : jb.bufs[(jb.first + it.s - 1) % 2];
-      load_box_async(src, jb.nx, jb.ny, 1, (int64_t)tx * kBX - kHaloX, (int64_t)ty * kBY - jb.r, 0,
+    if (it.s == 0 && !jb.tma0) {
+      load_box_async(jb.in, jb.nx, jb.ny, 1, (int64_t)tx * kBX - kHaloX, (int64_t)ty * kBY - jb.r, 0,
                      kBX + 2 * kHaloX, kBY + 2 * jb.r, 1, Sw, warp, kThreads / 32, lane);
       asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
     }
     const float* S = Sw;
-    float* dst = jb.bufs[(jb.first + it.s) % 2];
-    switch (jb.r) {
-      case 1: batch_tile<1>(jb, S, dst, tx * kBX, ty * kBY); break;
-      case 2: batch_tile<2>(jb, S, dst, tx * kBX, ty * kBY); break;
-      default: batch_tile<3>(jb, S, dst, tx * kBX, ty * kBY); break;
+    const bool last = it.s + 1 == jb.steps;
+    float* dst = last ? jb.out : jb.bufs[(jb.first + it.s) % 2];
+    const int64_t pitch = last ? jb.nx : jb.pitch;
+    const bool out_tf32 = !last;
+    if (it.s == 0) {
+      switch (jb.r) {
+        case 1: batch_tile<1, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+        case 2: batch_tile<2, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+        default: batch_tile<3, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+      }
+    } else {
+      switch (jb.r) {
+        case 1: batch_tile<1, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+        case 2: batch_tile<2, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+        default: batch_tile<3, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
+      }
     }
-    // all consumer stores of this tile, then one GPU-scope release of the
-    // tile's step counter (the barrier orders the other threads' stores
-    // before thread 0's release)
-    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // consumers only
-    if (tid == 0) {
-      st_release(jb.done + it.tile, it.s + 1);
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
-    }
+    // this warp is done with the stage and has issued its stores; the
+    // producer publishes the tile once all eight warps are here
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
   }
 }
 
@@ -306,21 +398,40 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       jb.tiles_x = (int)((p->nx + kBX - 1) / kBX);
       jb.tiles_y = (int)((p->ny + kBY - 1) / kBY);
       jb.steps = (int)steps[i];
-      jb.first = (steps[i] % 2 == 1) ? 0 : 1;
       jb.map0 = 3 * k;
       jb.a = reinterpret_cast<const uint4*>(p->dev.a_words);
       jb.meta = p->dev.meta_words;
-      jb.bufs[0] = outs[i];
-      jb.bufs[1] = p->dev.scratch;
+      jb.out = outs[i];
       jb.in = ins[i];
       jb.done = nullptr;
-      jb.tma = 1;
-      const float* bases[3] = {ins[i], outs[i], p->dev.scratch};
-      for (int m = 0; m < 3; ++m) {
-        std::memset(&maps[3 * k + m], 0, sizeof(CUtensorMap));
-        if (bases[m] == nullptr) { maps[3 * k + m] = maps[3 * k]; continue; }  // no scratch for 1-step jobs
-        if (!make_tensor_map(&maps[3 * k + m], bases[m], p->nx, p->ny, 1, kBX + 2 * kHaloX, kBY + 2 * p->r, 1))
-          jb.tma = 0;  // rows not 16-byte aligned: consumers load the box
+      const int box_x = kBX + 2 * kHaloX, box_y = kBY + 2 * p->r;
+      CUtensorMap* mp = &maps[3 * k];
+      std::memset(mp, 0, 3 * sizeof(CUtensorMap));
+      jb.tma0 = make_tensor_map(&mp[0], ins[i], p->nx, p->ny, 1, box_x, box_y, 1) ? 1 : 0;
+      const bool direct = jb.tma0 && make_tensor_map(&mp[1], outs[i], p->nx, p->ny, 1, box_x, box_y, 1) &&
+                          (steps[i] == 1 ||
+                           make_tensor_map(&mp[2], p->dev.scratch, p->nx, p->ny, 1, box_x, box_y, 1));
+      if (direct) {
+        jb.pitch = p->nx;
+        jb.first = (steps[i] % 2 == 1) ? 0 : 1;
+        jb.bufs[0] = outs[i];
+        jb.bufs[1] = p->dev.scratch;
+        if (steps[i] == 1) mp[2] = mp[0];
+      } else {
+        jb.pitch = (p->nx + 3) / 4 * 4;
+        jb.first = 0;
+        jb.bufs[0] = jb.bufs[1] = nullptr;
+        if (steps[i] > 1) {
+          const size_t grid_bytes = (size_t)jb.pitch * (size_t)p->ny * 4;
+          st = ensure_plan_pad(p, 2 * grid_bytes);
+          if (st != SPIDER_OK) return st;
+          jb.bufs[0] = p->dev.pad;
+          jb.bufs[1] = p->dev.pad + grid_bytes / 4;
+          for (int m = 0; m < 2; ++m)
+            if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, jb.pitch, box_x, box_y))
+              return fail(SPIDER_ERR_CUDA, "tensor map of a padded grid");
+        }
+        if (!jb.tma0) mp[0] = steps[i] > 1 ? mp[1] : mp[0];  // unused: the consumers load step 0
       }
       tiles[k] = (long long)jb.tiles_x * jb.tiles_y;
       total_tiles += tiles[k];
@@ -397,7 +508,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     });
     if (attr_err != cudaSuccess) return fail(SPIDER_ERR_CUDA, "batch kernel attributes");
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads + 32, smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads + 64, smem_bytes);
     const long long total_items = step_off[max_steps];
     const int grid = (int)std::max<long long>(
         1, std::min<long long>(total_items, (long long)std::max(occ, 1) * device_sm_count()));
@@ -431,7 +542,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       cudaKernelNodeParams kp = {};
       kp.func = reinterpret_cast<void*>(batch_kernel);
       kp.gridDim = dim3(grid);
-      kp.blockDim = dim3(kThreads + 32);
+      kp.blockDim = dim3(kThreads + 64);
       kp.sharedMemBytes = smem_bytes;
       kp.kernelParams = kargs;
       e = cudaGraphAddKernelNode(&kern, graph, &reset, 1, &kp);

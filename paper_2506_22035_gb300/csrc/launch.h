@@ -57,6 +57,11 @@ cudaError_t launch_fused3d_sp_tf32(int r, int T, const LaunchCtx& ctx);
 // grid cannot be described (row pitch or base not 16-byte aligned).
 bool make_tensor_map(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int box_x, int box_y,
                      int box_z);
+// The same for a 2-D grid (ny, nx) whose rows start `pitch` floats apart
+// (pitch >= nx, pitch * 4 a multiple of 16): box elements at x >= nx read as
+// zero, so whatever the row padding holds is never loaded.
+bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t pitch, int box_x,
+                             int box_y);
 
 int device_sm_count();
 

@@ -76,6 +76,8 @@ struct DeviceState {
   uint32_t* meta_words = nullptr;  // packed metadata
   float* w_dense = nullptr;        // dense coefficient cube (CUDA-core engine)
   float* scratch = nullptr;        // ping-pong grid
+  float* pad = nullptr;            // two row-padded ping-pong grids (spider_batch)
+  size_t pad_bytes = 0;
   float* host_stage_in = nullptr;  // device grids for spider_run_host
   float* host_stage_out = nullptr;
   int* status = nullptr;           // device error word (0 = ok)
@@ -134,5 +136,7 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
 int max_steps_per_pass(const spider_plan_t* p);
 // api.cu: upload the plan's operands (and allocate its scratch grid) if needed.
 spider_status ensure_plan_device(spider_plan_t* p, bool scratch);
+// api.cu: make the plan's padded ping-pong area at least `bytes` long.
+spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes);
 
 }  // namespace spider

@@ -470,6 +470,46 @@ def test_batch_persistent_queue_matches_individual_runs():
         p.close()
 
 
+def _offset_view(t, off):
+    """A copy of `t` that starts `off` floats into its own allocation (a base
+    address that is not 16-byte aligned when off % 4 != 0)."""
+    buf = torch.empty(t.numel() + off, dtype=t.dtype, device=t.device)
+    v = buf[off:].view(t.shape)
+    v.copy_(t)
+    return v
+
+
+def test_batch_ragged_rows_and_unaligned_buffers():
+    # rows of nx % 4 != 0 floats, or a grid that does not start on a 16-byte
+    # boundary, run in the plan's row-padded grids after the first step; the
+    # results are the plan's own, bit for bit, for 1, 2, 3 and more steps
+    g = np.random.default_rng(31)
+    cases = [((70, 130), 1, "box", 1, 0, 0), ((129, 301), 2, "star", 2, 0, 0), ((64, 129), 3, "box", 3, 0, 0),
+             ((200, 387), 1, "star", 8, 0, 0), ((65, 3), 1, "box", 5, 0, 0), ((96, 256), 2, "box", 4, 0, 1),
+             ((96, 256), 3, "star", 5, 1, 0), ((77, 1001), 3, "box", 6, 3, 2)]
+    plans, ins, outs, refs, steps, ws = [], [], [], [], [], []
+    for ext, r, kind, n, off_in, off_out in cases:
+        u0 = g.uniform(-1, 1, ext).astype(np.float32)
+        w = si.normalised_coeffs(2, r, kind, g)
+        ws.append(w)
+        plans.append(spider.Plan(w, ext, kind, "tf32"))
+        ins.append(_offset_view(torch.from_numpy(u0).cuda(), off_in))
+        outs.append(_offset_view(torch.full(ext, float("nan"), device="cuda"), off_out))
+        refs.append(gpu_run(u0, w, n, kind, "tf32"))
+        steps.append(n)
+    for _ in range(2):  # the second call reuses the padded grids
+        for o in outs:
+            o.fill_(float("nan"))
+        spider.batch(plans, ins, outs, steps)
+        torch.cuda.synchronize()
+        for k in range(len(cases)):
+            assert np.array_equal(outs[k].cpu().numpy(), refs[k]), cases[k]
+    u0 = ins[3].cpu().numpy()
+    check_close(outs[3].cpu().numpy(), oracle.stencil(u0, ws[3], 8), ("sparse_tc", "tf32"))
+    for p in plans:
+        p.close()
+
+
 def test_batch_with_direct_jobs_and_precisions():
     # jobs the queue does not take (3-D, split precision, rows not 16-byte
     # aligned) run through their own plans in the same call
