@@ -105,7 +105,8 @@ static spider_status ensure_scratch(spider_plan_t* p) {
 
 spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes) {
   if (p->dev.pad && p->dev.pad_bytes >= bytes) return SPIDER_OK;
-  cudaFree(p->dev.pad);  // waits for the device: no earlier batch still uses it
+  cudaFree(p->dev.pad);  // waits for the device: no earlier run still uses it
+  if (p->dev.pad) drop_graphs(p);  // cached run graphs hold the old address
   p->dev.pad = nullptr;
   p->dev.pad_bytes = 0;
   cudaError_t e = cudaMalloc(&p->dev.pad, bytes);
@@ -138,46 +139,80 @@ int max_steps_per_pass(const spider_plan_t* p) {
   return 1;
 }
 
+// A run of a 2-D or 3-D grid steps through the plan's padded grids when
+// `out` is not a TMA-describable grid in the packed layout.
+static bool run_is_padded(const spider_plan_t* p, const float* out, int64_t steps) {
+  return p->ndim >= 2 && steps > 1 && !(p->nx % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0);
+}
+static int64_t padded_pitch(const spider_plan_t* p) { return (p->nx + 3) / 4 * 4; }
+
+// Every buffer a run of `steps` steps into `out` needs (operands, scratch
+// grid, padded grids), allocated before its launches are issued or captured.
+static spider_status ensure_run_buffers(spider_plan_t* p, const float* out, int64_t steps) {
+  spider_status s = ensure_device(p);
+  if (s == SPIDER_OK && steps > 1) s = ensure_scratch(p);
+  if (s == SPIDER_OK && run_is_padded(p, out, steps))
+    s = ensure_plan_pad(p, 2 * (size_t)padded_pitch(p) * (size_t)p->ny * (size_t)p->nz * sizeof(float));
+  return s;
+}
+
 spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
   const size_t bytes = (size_t)p->points() * sizeof(float);
   if (steps == 0) {
     SPIDER_CUDA(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, stream));
     return SPIDER_OK;
   }
-  spider_status s = ensure_device(p);
+  spider_status s = ensure_run_buffers(p, out, steps);
   if (s != SPIDER_OK) return s;
-  if (steps > 1) {
-    s = ensure_scratch(p);
-    if (s != SPIDER_OK) return s;
-  }
   LaunchCtx ctx;
   ctx.plan = p;
   ctx.stream = stream;
   ctx.sms = device_sm_count();
-  // Passes of T fused time steps (2-D grids whose rows and buffers are
-  // 16-byte aligned, as TMA requires), then one pass with the remainder.
-  int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
   auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  if (T > 1 && !(p->nx % 4 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch))) T = 1;
-  if (T > 1 && p->ndim == 1 && p->nx % 8 != 0) T = 1;  // the 1-D fused kernel's TMA view
-  const int64_t full = steps / T;
-  const int rem = (int)(steps % T);
-  const int64_t npasses = full + (rem ? 1 : 0);
-  // Ping-pong between out and the scratch grid; the parity of the first
-  // destination makes the last pass land in out.
-  float* bufs[2] = {out, p->dev.scratch};
-  const int first = (npasses % 2 == 1) ? 0 : 1;
+  // TMA reads a grid whose rows are a multiple of 16 bytes from a 16-byte
+  // aligned base.  When out is not such a grid (rows of nx % 4 != 0 floats,
+  // or an unaligned caller buffer), the passes between
+  // the first and the last run in the plan's two padded grids (rows rounded
+  // up to 4 floats), so that every pass after the first reads through TMA
+  // and may fuse time steps; the first pass reads `in` as it is and the last
+  // writes `out` in the caller's packed layout.
+  const bool padded = run_is_padded(p, out, steps);
+  const bool in_tma = p->nx % 4 == 0 && aligned(in);
+  // Passes of T fused time steps, then one pass with the remainder; a first
+  // pass that cannot read `in` through TMA takes one step on its own.
+  int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
+  if (p->ndim == 1 && T > 1 && !(p->nx % 8 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch)))
+    T = 1;  // the 1-D fused kernel's TMA view of every grid
+  const int head = (T > 1 && !in_tma && p->ndim >= 2) ? 1 : 0;  // a single-step first pass
+  const int64_t body = steps - head;
+  const int64_t full = body / T;
+  const int rem = (int)(body % T);
+  const int64_t npasses = head + full + (rem ? 1 : 0);
+  auto pass_steps = [&](int64_t k) { return k < head ? 1 : (k - head < full ? T : rem); };
   // TF32 engines: every grid between two passes is stored rounded to TF32 as
   // the next pass would round it, and that pass skips the rounding; the
   // caller's input is rounded on load and the final grid is stored unrounded.
   const bool tf32 = p->engine == SPIDER_ENGINE_DENSE_TC ||
                     (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3);
+  float* bufs[2] = {out, p->dev.scratch};
+  int first = (npasses % 2 == 1) ? 0 : 1;  // packed: the last pass lands in out
+  int64_t pitch = p->nx;
+  if (padded) {
+    pitch = padded_pitch(p);
+    const size_t grid_bytes = (size_t)pitch * (size_t)p->ny * (size_t)p->nz * sizeof(float);
+    bufs[0] = p->dev.pad;
+    bufs[1] = p->dev.pad + grid_bytes / sizeof(float);
+    first = 0;
+  }
   for (int64_t k = 0; k < npasses; ++k) {
-    ctx.dst = bufs[(first + k) % 2];
+    const bool last = k + 1 == npasses;
+    ctx.dst = (padded && last) ? out : bufs[(first + k) % 2];
     ctx.src = (k == 0) ? in : bufs[(first + k - 1) % 2];
+    ctx.dst_pitch = (padded && !last) ? pitch : 0;
+    ctx.src_pitch = (padded && k > 0) ? pitch : 0;
     ctx.in_tf32 = tf32 && k > 0;
-    ctx.out_tf32 = tf32 && k + 1 < npasses;
-    cudaError_t e = launch_pass(ctx, k < full ? T : rem);
+    ctx.out_tf32 = tf32 && !last;
+    cudaError_t e = launch_pass(ctx, pass_steps(k));
     if (e == cudaErrorNotSupported) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil/engine");
     if (e != cudaSuccess) return cuda_fail(e, "stencil pass launch");
   }
@@ -234,8 +269,7 @@ static spider_status run_cached(spider_plan_t* p, const float* in, float* out, i
   }
   // second sight: capture
   hit->last_use = ++d.graph_clock;
-  spider_status s = ensure_device(p);
-  if (s == SPIDER_OK && steps > 1) s = ensure_scratch(p);
+  spider_status s = ensure_run_buffers(p, out, steps);
   if (s != SPIDER_OK) return s;
   if (!d.capture_stream) SPIDER_CUDA(cudaStreamCreateWithFlags(&d.capture_stream, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;

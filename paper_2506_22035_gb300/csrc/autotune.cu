@@ -22,6 +22,16 @@ Key key_of(const spider_plan_t* p) {
 }
 
 }  // namespace
+
+bool autotune_lookup(const spider_plan_t* p, int* steps_per_pass, int* variant) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto it = g_cache.find(key_of(p));
+  if (it == g_cache.end()) return false;
+  *steps_per_pass = it->second.first;
+  *variant = it->second.second;
+  return true;
+}
+
 }  // namespace spider
 
 using namespace spider;

@@ -33,6 +33,7 @@ constexpr int kMaxStageFloats = (kBY + 2 * kMaxR) * (kBX + 2 * kHaloX);
 constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
 constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
 constexpr int kMaxTableSmem = 48 * 1024;
+constexpr long long kFuseMinPoints = 1LL << 21;  // grids this large run as fused passes of their own
 
 // Step s reads `in` (s = 0) or bufs[(first + s - 1) % 2] and writes `out`
 // (the last step) or bufs[(first + s) % 2].  When in, out and the plan's
@@ -368,15 +369,35 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return fail(SPIDER_ERR_INVALID, "a plan may appear once per batch (its scratch grid)");
   }
-  // Jobs the persistent queue handles: 2-D sparse TF32 with TMA-describable
-  // rows and at least one step.  Others run through their own plan, on the
-  // same stream, after the persistent launch.
-  std::vector<int> queued, direct;
+  // Jobs the persistent queue handles: 2-D sparse TF32, radius <= 3, at
+  // least one step, and fewer than kFuseMinPoints points.  Larger grids of
+  // several steps run first, as fused multi-step passes of their own (the
+  // plan's tuned depth, else the tuned depth of its kind, else 2 steps per
+  // pass): the queue takes one step per HBM pass.  The rest run through
+  // their own plan after the persistent launch.
+  std::vector<int> queued, fused, direct;
   for (int i = 0; i < n; ++i) {
     spider_plan_t* p = plans[i];
     const bool ok = p->ndim == 2 && p->r <= kMaxR && p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec == SPIDER_TF32 &&
                     steps[i] > 0;
-    (ok ? queued : direct).push_back(i);
+    const bool big = ok && steps[i] > 1 && p->points() >= kFuseMinPoints;
+    (big ? fused : ok ? queued : direct).push_back(i);
+  }
+  for (int i : fused) {
+    spider_plan_t* p = plans[i];
+    std::lock_guard<std::mutex> lock(p->mu);
+    const int old_T = p->steps_per_pass, old_v = p->tile_variant;
+    int T = old_T, v = old_v;
+    if (T < 2 && !autotune_lookup(p, &T, &v)) {
+      T = 2;
+      v = 0;
+    }
+    p->steps_per_pass = T;
+    p->tile_variant = v;
+    spider_status s = run_device(p, ins[i], outs[i], steps[i], stream);
+    p->steps_per_pass = old_T;
+    p->tile_variant = old_v;
+    if (s != SPIDER_OK) return s;
   }
   if (!queued.empty()) {
     const int nq = (int)queued.size();
@@ -428,7 +449,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
           jb.bufs[0] = p->dev.pad;
           jb.bufs[1] = p->dev.pad + grid_bytes / 4;
           for (int m = 0; m < 2; ++m)
-            if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, jb.pitch, box_x, box_y))
+            if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box_x, box_y, 1))
               return fail(SPIDER_ERR_CUDA, "tensor map of a padded grid");
         }
         if (!jb.tma0) mp[0] = steps[i] > 1 ? mp[1] : mp[0];  // unused: the consumers load step 0

@@ -72,7 +72,13 @@ struct spider_server_t {
 namespace spider {
 namespace {
 
-size_t job_bytes(const spider_plan_t* p) { return 3 * (size_t)p->points() * sizeof(float) + 65536; }
+size_t job_bytes(const spider_plan_t* p) {
+  // two grids of the job and the plan's scratch grid, plus its two padded
+  // grids when its rows are not a multiple of 4 floats
+  size_t b = 3 * (size_t)p->points() * sizeof(float) + 65536;
+  if (p->ndim >= 2 && p->nx % 4 != 0) b += 2 * (size_t)((p->nx + 3) / 4 * 4) * p->ny * p->nz * sizeof(float);
+  return b;
+}
 
 void finish(spider_server_t* s, Job* j, spider_status st, const std::string& err) {
   if (j->cur) cudaFree(j->cur);

@@ -117,14 +117,14 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
             d[yy * DP + (h ? p1 : p0)] = in ? acc[yy][h] : 0.f;
           }
       } else {
-        float* o = args.dst + (int64_t)gy0 * args.nx + gx0 + c.lane;
+        float* o = args.dst + (int64_t)gy0 * args.pitch + gx0 + c.lane;
 #pragma unroll
         for (int yy = 0; yy < F::H; ++yy)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const bool in = interior || ((unsigned)(gy0 + yy) < (unsigned)args.ny &&
                                          (unsigned)(gx0 + c.lane + 32 * h) < (unsigned)args.nx);
-            if (in) o[(int64_t)yy * args.nx + 32 * h] = acc[yy][h];
+            if (in) o[(int64_t)yy * args.pitch + 32 * h] = acc[yy][h];
           }
       }
     } else {
@@ -184,14 +184,14 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
         }
       } else {
         if (kStoreTF32 && args.out_tf32) round_tf32_inplace(acc);
-        float* o = args.dst + (int64_t)gy0 * args.nx + gx0 + lx;
-        const int nx = (int)args.nx;
+        float* o = args.dst + (int64_t)gy0 * args.pitch + gx0 + lx;
+        const int pitch = (int)args.pitch;
         if (interior) {
 #pragma unroll
           for (int pp = 0; pp < F::H / 2; ++pp)
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
-              float* orow = o + (size_t)(2 * pp + sr) * nx;
+              float* orow = o + (size_t)(2 * pp + sr) * pitch;
               orow[0] = acc[pp][2 * sr];
               orow[8] = acc[pp][2 * sr + 1];
             }
@@ -203,7 +203,7 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
               if ((unsigned)(gy0 + 2 * pp + sr) < (unsigned)args.ny) {
-                float* orow = o + (size_t)(2 * pp + sr) * nx;
+                float* orow = o + (size_t)(2 * pp + sr) * pitch;
                 if (xin0) orow[0] = acc[pp][2 * sr];
                 if (xin1) orow[8] = acc[pp][2 * sr + 1];
               }

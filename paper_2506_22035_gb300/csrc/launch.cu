@@ -30,31 +30,20 @@ EncodeTiledFn encode_fn() {
 
 bool make_tensor_map(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int box_x, int box_y,
                      int box_z) {
+  return make_tensor_map_pitched(map, base, nx, ny, nz, nx, box_x, box_y, box_z);
+}
+
+bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int64_t pitch,
+                             int box_x, int box_y, int box_z) {
   // TMA needs a 16-byte aligned base and row/plane pitches that are
   // multiples of 16 bytes.
-  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (nx * 4) % 16 != 0) return false;
-  if (nx >= (1LL << 32) || ny >= (1LL << 32) || nz >= (1LL << 32)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (pitch * 4) % 16 != 0 || pitch < nx) return false;
+  if (pitch >= (1LL << 32) || ny >= (1LL << 32) || nz >= (1LL << 32)) return false;
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)(nx * 4), (cuuint64_t)(nx * ny * 4)};
-  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
-bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t pitch, int box_x,
-                             int box_y) {
-  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (pitch * 4) % 16 != 0 || pitch < nx) return false;
-  if (pitch >= (1LL << 32) || ny >= (1LL << 32)) return false;
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 1};
   const cuuint64_t strides[2] = {(cuuint64_t)(pitch * 4), (cuuint64_t)(pitch * ny * 4)};
-  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -19,6 +19,10 @@ struct LaunchCtx {
   // is read by a later pass, so it may be stored rounded.
   bool in_tf32 = false;
   bool out_tf32 = false;
+  // Row pitches of src and dst in floats (0: nx, the packed layout).  A
+  // padded source must be TMA-describable; planes are ny * pitch apart.
+  int64_t src_pitch = 0;
+  int64_t dst_pitch = 0;
 };
 
 // Launches one time step src -> dst for the plan's engine and precision.
@@ -57,11 +61,11 @@ cudaError_t launch_fused3d_sp_tf32(int r, int T, const LaunchCtx& ctx);
 // grid cannot be described (row pitch or base not 16-byte aligned).
 bool make_tensor_map(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int box_x, int box_y,
                      int box_z);
-// The same for a 2-D grid (ny, nx) whose rows start `pitch` floats apart
-// (pitch >= nx, pitch * 4 a multiple of 16): box elements at x >= nx read as
-// zero, so whatever the row padding holds is never loaded.
-bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t pitch, int box_x,
-                             int box_y);
+// The same for a grid whose rows start `pitch` floats apart (pitch >= nx,
+// pitch * 4 a multiple of 16; planes ny * pitch apart): box elements at
+// x >= nx read as zero, so whatever the row padding holds is never loaded.
+bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int64_t nz, int64_t pitch,
+                             int box_x, int box_y, int box_z);
 
 int device_sm_count();
 

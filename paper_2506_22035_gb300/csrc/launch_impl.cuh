@@ -14,6 +14,15 @@
 
 namespace spider {
 
+// Row pitches of a pass's grids (LaunchCtx pitch 0 = nx) and the source's
+// tensor map in that layout.
+inline int64_t src_pitch(const LaunchCtx& ctx) { return ctx.src_pitch ? ctx.src_pitch : ctx.plan->nx; }
+inline int64_t dst_pitch(const LaunchCtx& ctx) { return ctx.dst_pitch ? ctx.dst_pitch : ctx.plan->nx; }
+inline bool make_src_map(CUtensorMap* map, const LaunchCtx& ctx, int64_t nz, int box_x, int box_y, int box_z) {
+  const spider_plan_t* p = ctx.plan;
+  return make_tensor_map_pitched(map, ctx.src, p->nx, p->ny, nz, src_pitch(ctx), box_x, box_y, box_z);
+}
+
 // Launch with programmatic stream serialization: the kernel may begin while
 // the previous kernel on the stream drains; the kernels wait (griddep_wait)
 // before touching the grids.
@@ -64,6 +73,7 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = p->nz;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
   a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
   a.tiles_z = (int)((p->nz + C::BZ - 1) / C::BZ);
@@ -73,7 +83,8 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   a.status = p->dev.status;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  a.use_tma = make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, C::SZ) ? 1 : 0;
+  a.use_tma = make_src_map(&map, ctx, p->nz, C::SX, C::SY, C::SZ) ? 1 : 0;
+  if (!a.use_tma && src_pitch(ctx) != p->nx) return cudaErrorNotSupported;  // the loader reads packed rows
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
@@ -120,7 +131,7 @@ cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, C::SX, C::SY, 1)) return cudaErrorNotSupported;
+  if (!make_src_map(&map, ctx, p->nz, C::SX, C::SY, 1)) return cudaErrorNotSupported;
   auto kern = stream3d_kernel<C, MODE, RIN, STAR>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
@@ -147,6 +158,7 @@ cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = p->nz;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
   a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
   a.tiles_z = 1;
@@ -225,7 +237,7 @@ cudaError_t launch_fused_cfg_k(const LaunchCtx& ctx) {
   if (p->ndim != 2) return cudaErrorNotSupported;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, 1, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
+  if (!make_src_map(&map, ctx, 1, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
   auto kern = fused_step_kernel<F, MODE, RIN>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
@@ -252,6 +264,7 @@ cudaError_t launch_fused_cfg_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = 1;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + F::BX - 1) / F::BX);
   a.tiles_y = (int)((p->ny + F::BY - 1) / F::BY);
   a.tiles_z = 1;
@@ -330,7 +343,7 @@ cudaError_t launch_fused3d_k(const LaunchCtx& ctx) {
   if (p->ndim != 3) return cudaErrorNotSupported;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  if (!make_tensor_map(&map, ctx.src, p->nx, p->ny, p->nz, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
+  if (!make_src_map(&map, ctx, p->nz, F::width(0), F::rows(0), 1)) return cudaErrorNotSupported;
   auto kern = stream3d_fused_kernel<F, MODE, RIN, STAR>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};
@@ -357,6 +370,7 @@ cudaError_t launch_fused3d_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = p->nz;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + F::BX - 1) / F::BX);
   a.tiles_y = (int)((p->ny + F::BY - 1) / F::BY);
   a.tiles_z = 1;
@@ -452,6 +466,7 @@ cudaError_t launch_wide_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = 1;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + C::BX - 1) / C::BX);
   a.tiles_y = (int)((p->ny + C::BY - 1) / C::BY);
   a.tiles_z = 1;
@@ -462,7 +477,8 @@ cudaError_t launch_wide_k(const LaunchCtx& ctx) {
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  a.use_tma = make_tensor_map(&map, ctx.src, p->nx, p->ny, 1, C::SX, C::SY, 1) ? 1 : 0;
+  a.use_tma = make_src_map(&map, ctx, 1, C::SX, C::SY, 1) ? 1 : 0;
+  if (!a.use_tma && src_pitch(ctx) != p->nx) return cudaErrorNotSupported;  // the loader reads packed rows
   const long long ntiles = (long long)a.tiles_x * a.tiles_y;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
@@ -500,6 +516,7 @@ cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = 1;
   a.nz = 1;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + C::NT - 1) / C::NT);
   a.tiles_y = 1;
   a.tiles_z = 1;
@@ -551,6 +568,7 @@ cudaError_t launch_wide1d_fused_k(const LaunchCtx& ctx) {
   a.nx = p->nx;
   a.ny = 1;
   a.nz = 1;
+  a.pitch = dst_pitch(ctx);
   a.tiles_x = (int)((p->nx + C::NT - 1) / C::NT);
   a.tiles_y = 1;
   a.tiles_z = 1;

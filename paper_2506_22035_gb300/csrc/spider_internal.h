@@ -136,6 +136,9 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
 int max_steps_per_pass(const spider_plan_t* p);
 // api.cu: upload the plan's operands (and allocate its scratch grid) if needed.
 spider_status ensure_plan_device(spider_plan_t* p, bool scratch);
+// autotune.cu: the tuned (steps per pass, tile variant) of the plan's kind
+// of stencil, if one has been measured.
+bool autotune_lookup(const spider_plan_t* p, int* steps_per_pass, int* variant);
 // api.cu: make the plan's padded ping-pong area at least `bytes` long.
 spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes);
 

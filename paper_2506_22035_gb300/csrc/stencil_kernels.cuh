@@ -38,6 +38,7 @@ struct StepArgs {
   const float* src;        // source grid (generic loader only)
   float* dst;              // destination grid
   int64_t nx, ny, nz;
+  int64_t pitch;           // destination row pitch in floats (>= nx); planes are ny * pitch apart
   int tiles_x, tiles_y, tiles_z;
   const uint4* a_words;    // packed A operands
   const uint32_t* meta;    // packed metadata
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(C::kThreads)
         }
       }
       if (z < args.nz) {
-        float* o = args.dst + (z * args.ny + ybase) * args.nx + xbase + lane;
-        const int nx = (int)args.nx;
+        float* o = args.dst + (z * args.ny + ybase) * args.pitch + xbase + lane;
+        const int pitch = (int)args.pitch;
         const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
         const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
 #pragma unroll
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(C::kThreads)
           if (yy < ylim) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-              if (lane + 32 * c < xlim) o[(size_t)yy * nx + 32 * c] = acc[yy][c];
+              if (lane + 32 * c < xlim) o[(size_t)yy * pitch + 32 * c] = acc[yy][c];
           }
         }
       }
@@ -391,15 +392,15 @@ __global__ void __launch_bounds__(C::kThreads)
       }
       if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
       if (z < args.nz) {
-        float* o = args.dst + (z * args.ny + ybase) * args.nx + xbase + 16 * q + g;
-        const int nx = (int)args.nx;
+        float* o = args.dst + (z * args.ny + ybase) * args.pitch + xbase + 16 * q + g;
+        const int pitch = (int)args.pitch;
         if (ybase + C::H <= args.ny && xbase + 64 <= args.nx) {
           // interior warp tile: no bounds checks
 #pragma unroll
           for (int pp = 0; pp < C::H / 2; ++pp) {
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
-              float* orow = o + (size_t)(2 * pp + sr) * nx;
+              float* orow = o + (size_t)(2 * pp + sr) * pitch;
               orow[0] = acc[pp][2 * sr];
               orow[8] = acc[pp][2 * sr + 1];
             }
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(C::kThreads)
               if (2 * pp + sr < ylim) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c)
-                  if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * nx + 8 * c] = acc[pp][2 * sr + c];
+                  if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * pitch + 8 * c] = acc[pp][2 * sr + c];
               }
             }
           }

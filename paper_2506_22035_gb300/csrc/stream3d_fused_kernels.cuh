@@ -160,14 +160,14 @@ __device__ __forceinline__ void f3_level(Fuse3Ctx& c, int zi, const uint4 (&A)[2
         }
       } else {
         if (args.out_tf32) round_tf32_inplace(acc);
-        float* o = args.dst + ((int64_t)zt * args.ny + gy0) * args.nx + gx0 + lx;
-        const int nx = (int)args.nx;
+        float* o = args.dst + ((int64_t)zt * args.ny + gy0) * args.pitch + gx0 + lx;
+        const int pitch = (int)args.pitch;
         if (interior) {
 #pragma unroll
           for (int pp = 0; pp < H / 2; ++pp)
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
-              float* orow = o + (size_t)(2 * pp + sr) * nx;
+              float* orow = o + (size_t)(2 * pp + sr) * pitch;
               orow[0] = acc[pp][2 * sr];
               orow[8] = acc[pp][2 * sr + 1];
             }
@@ -179,7 +179,7 @@ __device__ __forceinline__ void f3_level(Fuse3Ctx& c, int zi, const uint4 (&A)[2
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
               if ((unsigned)(gy0 + 2 * pp + sr) < (unsigned)args.ny) {
-                float* orow = o + (size_t)(2 * pp + sr) * nx;
+                float* orow = o + (size_t)(2 * pp + sr) * pitch;
                 if (xin0) orow[0] = acc[pp][2 * sr];
                 if (xin1) orow[8] = acc[pp][2 * sr + 1];
               }

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
             }
           }
         }
-        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.nx + xbase + lane;
+        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.pitch + xbase + lane;
         const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
         const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
 #pragma unroll
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           if (yy < ylim) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-              if (lane + 32 * c < xlim) o[(size_t)yy * args.nx + 32 * c] = acc[yy][c];
+              if (lane + 32 * c < xlim) o[(size_t)yy * args.pitch + 32 * c] = acc[yy][c];
           }
       } else {
         float acc[C::H / 2][4];
@@ -218,14 +218,14 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
             for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
         }
         if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
-        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.nx + xbase + 16 * q + g;
-        const int nx = (int)args.nx;
+        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.pitch + xbase + 16 * q + g;
+        const int pitch = (int)args.pitch;
         if (ybase + C::H <= args.ny && xbase + 64 <= args.nx) {
 #pragma unroll
           for (int pp = 0; pp < C::H / 2; ++pp)
 #pragma unroll
             for (int sr = 0; sr < 2; ++sr) {
-              float* orow = o + (size_t)(2 * pp + sr) * nx;
+              float* orow = o + (size_t)(2 * pp + sr) * pitch;
               orow[0] = acc[pp][2 * sr];
               orow[8] = acc[pp][2 * sr + 1];
             }
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
               if (2 * pp + sr < ylim) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c)
-                  if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * nx + 8 * c] = acc[pp][2 * sr + c];
+                  if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * pitch + 8 * c] = acc[pp][2 * sr + c];
               }
         }
       }

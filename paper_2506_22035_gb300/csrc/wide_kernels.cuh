@@ -159,12 +159,12 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
     const int ybase = y0 + wy * C::H;
     const int xb = x0 + 32 * q + g;
     const int cols[4] = {xb, xb + 16, xb + 8, xb + 24};
-    float* o = args.dst + (int64_t)ybase * args.nx;
+    float* o = args.dst + (int64_t)ybase * args.pitch;
     const bool interior = ybase + C::H <= args.ny && x0 + C::BX <= args.nx;
 #pragma unroll
     for (int yy = 0; yy < C::H; ++yy) {
       if (interior || ybase + yy < args.ny) {
-        float* orow = o + (int64_t)yy * args.nx;
+        float* orow = o + (int64_t)yy * args.pitch;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (interior || cols[j] < args.nx) orow[cols[j]] = acc[yy][j];
