@@ -151,8 +151,14 @@ spider_status spider_plan_operands(spider_plan plan, uint32_t* operand_words, si
  *  steps     >= 0.
  *  stream    CUDA stream (0 = legacy default stream).
  * The library ping-pongs between grid_out and a plan-owned scratch grid, so
- * any step count ends in grid_out.  Calls on one plan must not overlap on the
- * GPU (the scratch grid is shared); use one plan per concurrent stream. */
+ * any step count ends in grid_out.  When grid_out cannot be read by TMA in
+ * its own layout (2-D and 3-D grids whose rows are not a multiple of 4
+ * floats, or a grid_out that is not 16-byte aligned), the steps between the
+ * first and the last run in two plan-owned grids whose rows are padded to a
+ * multiple of 4 floats, allocated on first use (2 * ny * nz * round4(nx)
+ * floats); grid_in and grid_out keep the caller's packed layout.  Calls on
+ * one plan must not overlap on the GPU (its scratch grids are shared); use
+ * one plan per concurrent stream. */
 spider_status spider_run(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
                          cudaStream_t stream);
 
@@ -199,9 +205,14 @@ void spider_plan_destroy(spider_plan plan);
  * issued as a CUDA graph: work items (time step, grid, 64 x 128 tile) are
  * claimed from a device queue in step-major order, and step s of a tile
  * starts only after the tile and its eight neighbours finished step s-1
- * (per-tile counters, bounded waits).  Other plans (3-D, split precisions,
- * comparator engines) run through spider_run on the same stream after it.
- * Synchronous: returns when all grids are done.  n <= 4096.
+ * (per-tile counters, bounded waits).  Such grids of at least 2^21 points
+ * and more than one step run first, through spider_run with fused passes
+ * (the plan's steps per pass if above 1, else the autotuned choice of its
+ * kind of stencil, else 2).  Other plans (3-D, split precisions, comparator
+ * engines, radius above 3) run through spider_run on the same stream after
+ * the persistent launch.  Grids whose rows are not a multiple of 4 floats,
+ * or whose buffers are not 16-byte aligned, use the plan's padded grids (see
+ * spider_run).  Synchronous: returns when all grids are done.  n <= 4096.
  * SPIDER_ERR_TIMEOUT if a dependency wait ran out. */
 spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                            const int64_t* steps, cudaStream_t stream);
