@@ -110,7 +110,13 @@ spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes) {
   p->dev.pad = nullptr;
   p->dev.pad_bytes = 0;
   cudaError_t e = cudaMalloc(&p->dev.pad, bytes);
+  // zero once: the kernels never store beyond nx, so the 1-D grids' tails
+  // stay zero and read as the halo
+  if (e == cudaSuccess) e = cudaMemset(p->dev.pad, 0, bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();  // before any stream of the caller writes it
   if (e != cudaSuccess) {
+    cudaFree(p->dev.pad);
+    p->dev.pad = nullptr;
     cudaGetLastError();
     return fail(SPIDER_ERR_OOM, std::string("padded grids: ") + cudaGetErrorString(e));
   }
@@ -139,12 +145,19 @@ int max_steps_per_pass(const spider_plan_t* p) {
   return 1;
 }
 
-// A run of a 2-D or 3-D grid steps through the plan's padded grids when
-// `out` is not a TMA-describable grid in the packed layout.
+// A run steps through the plan's padded grids when `out` is not a grid TMA
+// can read in its packed layout: 2-D and 3-D rows of a multiple of 4
+// floats, 1-D arrays (read as rows of 8 floats) of a multiple of 8, and a
+// 16-byte aligned base.
+static int tma_multiple(const spider_plan_t* p) { return p->ndim == 1 ? 8 : 4; }
 static bool run_is_padded(const spider_plan_t* p, const float* out, int64_t steps) {
-  return p->ndim >= 2 && steps > 1 && !(p->nx % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  return steps > 1 && !(p->nx % tma_multiple(p) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0);
 }
-static int64_t padded_pitch(const spider_plan_t* p) { return (p->nx + 3) / 4 * 4; }
+// Row pitch (1-D: length) of the padded grids.
+static int64_t padded_pitch(const spider_plan_t* p) {
+  const int m = tma_multiple(p);
+  return (p->nx + m - 1) / m * m;
+}
 
 // Every buffer a run of `steps` steps into `out` needs (operands, scratch
 // grid, padded grids), allocated before its launches are issued or captured.
@@ -169,21 +182,19 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   ctx.stream = stream;
   ctx.sms = device_sm_count();
   auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  // TMA reads a grid whose rows are a multiple of 16 bytes from a 16-byte
-  // aligned base.  When out is not such a grid (rows of nx % 4 != 0 floats,
-  // or an unaligned caller buffer), the passes between
+  // TMA reads a grid whose rows are a multiple of 16 bytes (1-D: whose
+  // length is a multiple of 8 floats) from a 16-byte aligned base.  When out
+  // is not such a grid, the passes between
   // the first and the last run in the plan's two padded grids (rows rounded
   // up to 4 floats), so that every pass after the first reads through TMA
   // and may fuse time steps; the first pass reads `in` as it is and the last
   // writes `out` in the caller's packed layout.
   const bool padded = run_is_padded(p, out, steps);
-  const bool in_tma = p->nx % 4 == 0 && aligned(in);
+  const bool in_tma = p->nx % tma_multiple(p) == 0 && aligned(in);
   // Passes of T fused time steps, then one pass with the remainder; a first
   // pass that cannot read `in` through TMA takes one step on its own.
-  int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
-  if (p->ndim == 1 && T > 1 && !(p->nx % 8 == 0 && aligned(in) && aligned(out) && aligned(p->dev.scratch)))
-    T = 1;  // the 1-D fused kernel's TMA view of every grid
-  const int head = (T > 1 && !in_tma && p->ndim >= 2) ? 1 : 0;  // a single-step first pass
+  const int T = std::min(p->steps_per_pass, max_steps_per_pass(p));
+  const int head = (T > 1 && !in_tma) ? 1 : 0;  // a single-step first pass
   const int64_t body = steps - head;
   const int64_t full = body / T;
   const int rem = (int)(body % T);

@@ -527,8 +527,11 @@ cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  // the array as rows of 8 floats (needs a length that is a multiple of 8)
-  a.use_tma = (p->nx % 8 == 0 && make_tensor_map(&map, ctx.src, 8, p->nx / 8, 1, 8, C::kBoxRows, 1)) ? 1 : 0;
+  // the array as rows of 8 floats (needs a length that is a multiple of 8;
+  // a padded source is src_pitch long, its tail beyond nx zero)
+  const int64_t len = src_pitch(ctx);
+  a.use_tma = (len % 8 == 0 && make_tensor_map(&map, ctx.src, 8, len / 8, 1, 8, C::kBoxRows, 1)) ? 1 : 0;
+  if (!a.use_tma && len != p->nx) return cudaErrorNotSupported;  // the loader reads nx points
   const int grid = (int)std::min<long long>(a.tiles_x, (long long)occ * ctx.sms);
   return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
 }
@@ -538,10 +541,11 @@ cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
 template <class C, bool RIN>
 cudaError_t launch_wide1d_fused_k(const LaunchCtx& ctx) {
   const spider_plan_t* p = ctx.plan;
-  if (p->nx % 8 != 0) return cudaErrorNotSupported;
+  const int64_t len = src_pitch(ctx);  // a padded source: its tail beyond nx is zero
+  if (len % 8 != 0) return cudaErrorNotSupported;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  if (!make_tensor_map(&map, ctx.src, 8, p->nx / 8, 1, 8, C::kBoxRows, 1)) return cudaErrorNotSupported;
+  if (!make_tensor_map(&map, ctx.src, 8, len / 8, 1, 8, C::kBoxRows, 1)) return cudaErrorNotSupported;
   auto kern = wide1d_fused_kernel<C, RIN>;
   static std::mutex mu;
   static int occ_by_dev[64] = {0};

@@ -383,8 +383,8 @@ def test_fused_1d_passes_match_single_steps(r, n):
     # 1-D passes compute every level on the tile's rows plus one neighbour row
     # each side; margins never reach the output rows and points outside the
     # array are zero at every level: bit-identical to single steps.  1792 is
-    # one tile, 96 less than a row, 2052 not a multiple of 8 (one step per
-    # pass, the fused kernel's TMA view needs multiples of 8).
+    # one tile, 96 less than a row, 2052 not a multiple of 8 (the passes after
+    # the first run in the plan's padded arrays, read as rows of 8 floats).
     g = si.rng(19, r)
     u0 = si.grid((n,), -1, 1, g)
     w = si.normalised_coeffs(1, r, "box", g)

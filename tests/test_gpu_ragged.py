@@ -142,3 +142,43 @@ def test_ragged_rows_graph_replay_and_batch_share_padded_grids():
             spider.batch([plan], [a], [b], [7])
             torch.cuda.synchronize()
     plan.close()
+
+
+@pytest.mark.parametrize("n", [3001, 4099, 10245, 130, 7])
+@pytest.mark.parametrize("r", [1, 3, 7])
+def test_1d_lengths_not_multiple_of_8(n, r):
+    # 1-D arrays are read through TMA as rows of 8 floats; other lengths run
+    # in the plan's padded arrays (zero tail) after the first pass.  Nine
+    # one-step calls never use the padded arrays (a single step reads the
+    # caller's array and writes the caller's array): the padded runs must
+    # reproduce them bit for bit.
+    g = si.rng(46, n % 97 + r)
+    u0 = si.grid((n,), -1, 1, g)
+    w = si.normalised_coeffs(1, r, "box", g)
+    plan = spider.Plan(w, (n,), "box", "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    for _ in range(9):
+        plan.run(a, b, 1)
+        a, b = b, a
+    torch.cuda.synchronize()
+    chain = a.cpu().numpy()
+    plan.close()
+    for T in (1, 2, 4):
+        assert np.array_equal(run(u0, w, 9, T=T), chain), T
+    assert np.array_equal(run(u0, w, 9, T=3, off_in=1, off_out=2), chain)
+    if n >= 64:  # a few points of mixed sign cancel: relative error is not TF32's there
+        close(chain, oracle.stencil(u0, w, 9))
+
+
+def test_1d_integer_exact_and_other_engines():
+    g = np.random.default_rng(47)
+    u = g.integers(-1, 2, size=(5003,)).astype(np.float32)
+    w = np.zeros(7, np.float32)
+    w[[0, 3, 5]] = [1.0, -1.0, 1.0]
+    ref = oracle.stencil(u, w, 6)
+    assert np.max(np.abs(ref)) < 2048
+    for T in (1, 2, 4):
+        assert np.array_equal(run(u, w, 6, T=T).astype(np.float64), ref), T
+    for engine, prec in (("cuda_core", "tf32"), ("sparse_tc", "f16x2"), ("dense_tc", "tf32")):
+        assert np.array_equal(run(u, w, 6, "box", prec, engine).astype(np.float64), ref), (engine, prec)
