@@ -104,10 +104,12 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
 /* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4
- * for 2-D stencils of radius 1..3, and with the sparse engine in TF32 for
- * 3-D radius-1 and 1-D plans; 1 otherwise.  Values the build does not support for the plan's stencil
- * return SPIDER_ERR_UNSUPPORTED.  Grids whose rows TMA cannot describe run
- * one step per pass whatever the setting. */
+ * for 2-D stencils of radius 1..3 (1..10 for radius 1 with the sparse
+ * engine in TF32: 5..10 run on small tiles, for grids too small to fill the
+ * GPU), and with the sparse engine in TF32 1..4 for 3-D radius-1 and 1-D
+ * plans; 1 otherwise.  Values the build does not support for the plan's
+ * stencil return SPIDER_ERR_UNSUPPORTED.  A run whose input grid TMA cannot
+ * read takes its first step on its own. */
 spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pass);
 
 /* Tile shape of the fused kernels.  2-D: 0 = warp units of 8 output rows and
@@ -122,8 +124,9 @@ spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pas
 spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 
 /* spider_plan_autotune -- measures the plan's configurations on the caller's
- * grids and keeps the fastest: time steps per pass 1..4 (where built, see
- * spider_plan_set_steps_per_pass) and the tile variant.  Each candidate runs
+ * grids and keeps the fastest: time steps per pass (1..4 where built, see
+ * spider_plan_set_steps_per_pass; up to 10, and at most `steps`, for
+ * radius-1 2-D grids of at most 2^22 points) and the tile variant.  Each candidate runs
  * `steps` steps from grid_in into
  * grid_out (device grids as for spider_run; grid_out is overwritten) once to
  * warm up and twice timed with CUDA events on `stream`; the call is

@@ -139,8 +139,8 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
 int max_steps_per_pass(const spider_plan_t* p) {
   if (p->wide()) return p->ndim == 1 ? 4 : 1;
-  if (p->ndim == 2) return 4;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
+  if (p->ndim == 2) return (p->r == 1 && sparse_tf32) ? 10 : 4;  // radius 1: deep tiles for 5..10
   if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
   return 1;
 }
@@ -398,7 +398,8 @@ spider_status spider_plan_set_steps_per_pass(spider_plan p, int steps_per_pass) 
   if (steps_per_pass < 1) return fail(SPIDER_ERR_INVALID, "steps_per_pass must be >= 1");
   if (steps_per_pass > max_steps_per_pass(p))
     return fail(SPIDER_ERR_UNSUPPORTED,
-                "temporal fusion is built for 2-D stencils and for 3-D radius-1 sparse TF32 plans, 2..4 steps per pass");
+                "temporal fusion is built for 2-D stencils (2..4 steps per pass; 2..10 for radius 1 in sparse TF32) "
+                "and for 3-D radius-1 and 1-D sparse TF32 plans (2..4)");
   p->steps_per_pass = steps_per_pass;
   return SPIDER_OK;
 }

@@ -74,12 +74,16 @@ extern "C" spider_status spider_plan_autotune(spider_plan p, const float* grid_i
   float best_ms = 1e30f;
   int best_T = 1, best_v = 0;
   spider_status st = SPIDER_OK;
+  // variant 4 (small 2-D tiles) only where the grid cannot fill the GPU
+  // with the 64-row tiles; more than 4 steps per pass (deep radius-1 tiles)
+  // only there too, and for at most the run's step count, with the small
+  // tile for the remainder pass
+  const bool small2d = p->ndim == 2 && p->points() <= (int64_t(1) << 22);
   for (int T = 1; T <= maxT && st == SPIDER_OK; ++T) {
-    // variant 4 (small 2-D tiles) only where the grid cannot fill the GPU
-    // with the 64-row tiles
-    const bool small2d = p->ndim == 2 && p->points() <= (int64_t(1) << 22);
+    if (T > 4 && (!small2d || T > steps)) break;
+    const int v0 = T > 4 ? 4 : 0;
     const int nv = T == 1 ? 1 : small2d ? 5 : 4;
-    for (int v = 0; v < nv && st == SPIDER_OK; ++v) {
+    for (int v = v0; v < nv && st == SPIDER_OK; ++v) {
       p->steps_per_pass = T;
       p->tile_variant = v;
       st = run_device(p, grid_in, grid_out, steps, stream);  // warm-up

@@ -81,7 +81,8 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     assert lib.spider_run(p.handle, ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), -1, None) == \
         _native.SPIDER_ERR_INVALID
     assert lib.spider_plan_set_steps_per_pass(p.handle, 0) == _native.SPIDER_ERR_INVALID
-    assert lib.spider_plan_set_steps_per_pass(p.handle, 5) == _native.SPIDER_ERR_UNSUPPORTED
+    assert lib.spider_plan_set_steps_per_pass(p.handle, 11) == _native.SPIDER_ERR_UNSUPPORTED
+    assert lib.spider_plan_set_steps_per_pass(p.handle, 10) == _native.SPIDER_OK   # radius 1: deep tiles
     assert lib.spider_plan_set_steps_per_pass(p.handle, 3) == _native.SPIDER_OK
     assert lib.spider_plan_set_tile_variant(p.handle, 5) == _native.SPIDER_ERR_INVALID
     assert lib.spider_plan_set_tile_variant(p.handle, 4) == _native.SPIDER_OK

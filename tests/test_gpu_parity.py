@@ -395,6 +395,36 @@ def test_fused_1d_passes_match_single_steps(r, n):
     check_close(single, oracle.stencil(u0, w, 9), ("sparse_tc", "tf32"))
 
 
+@pytest.mark.parametrize("kind", ["star", "box"])
+@pytest.mark.parametrize("shape,steps", [((512, 512), 10), ((130, 333), 23), ((40, 70), 7), ((1, 200), 12)])
+def test_deep_fusion_radius_1_matches_single_steps(kind, shape, steps):
+    # radius 1 in sparse TF32 fuses up to 10 steps per pass on 16 x 64 output
+    # tiles; each level is the one-step unit, so every depth (and the
+    # remainder pass with the small tile) reproduces single steps bit for bit
+    g = si.rng(23, steps)
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(2, 1, kind, g)
+    single = gpu_run(u0, w, steps, kind, "tf32", "sparse_tc", 1)
+    check_close(single, oracle.stencil(u0, w, steps), ("sparse_tc", "tf32"))
+    for T in (5, 6, 7, 8, 9, 10):
+        fused = gpu_run(u0, w, steps, kind, "tf32", "sparse_tc", T, 4)
+        assert np.array_equal(fused, single), (shape, steps, T)
+
+
+def test_deep_fusion_limits():
+    w = si.normalised_coeffs(2, 1, "star", si.rng(24, 0))
+    p = spider.Plan(w, (64, 64), "star", "tf32")
+    p.set_steps_per_pass(10)
+    with pytest.raises(spider.SpiderError):
+        p.set_steps_per_pass(11)
+    p.close()
+    w2 = si.normalised_coeffs(2, 2, "star", si.rng(24, 1))
+    p2 = spider.Plan(w2, (64, 64), "star", "tf32")
+    with pytest.raises(spider.SpiderError):
+        p2.set_steps_per_pass(5)  # deep tiles are built for radius 1 only
+    p2.close()
+
+
 @pytest.mark.parametrize("T", [2, 3, 4])
 def test_fused_parity_with_oracle(T):
     u0, w = si.workload_inputs(si.BOX2D_R3_8192, extents=(256, 1000))
