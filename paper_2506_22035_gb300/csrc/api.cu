@@ -140,7 +140,7 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 int max_steps_per_pass(const spider_plan_t* p) {
   if (p->wide()) return p->ndim == 1 ? 4 : 1;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
-  if (p->ndim == 2) return (p->r == 1 && sparse_tf32) ? 10 : 4;  // radius 1: deep tiles for 5..10
+  if (p->ndim == 2) return sparse_tf32 ? max_deep_steps(p->r) : 4;  // deep tiles beyond 4
   if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
   return 1;
 }

@@ -5,7 +5,7 @@
 
 namespace spider {
 cudaError_t launch_fused_sp_tf32_r1(int T, const LaunchCtx& ctx) {
-  if (T > 4) return launch_fused_deep<Mode::SpTF32>(T, ctx);  // 5..10 steps per pass
+  if (T > 4) return launch_fused_deep<Mode::SpTF32, 1>(T, ctx);  // 5..10 steps per pass
   return launch_fused_r<Mode::SpTF32, 1>(T, ctx);
 }
 }  // namespace spider

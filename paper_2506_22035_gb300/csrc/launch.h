@@ -56,6 +56,13 @@ cudaError_t launch_fused_cuda_core(int r, int T, const LaunchCtx& ctx);
 // modes, TMA-describable grids).
 cudaError_t launch_fused3d_sp_tf32(int r, int T, const LaunchCtx& ctx);
 
+// Deepest 2-D fusion built for the sparse TF32 mode: radius 1 up to 10 steps
+// per pass (deep tiles of 5..10 for small grids), radius 2 and 3 up to 4.
+// Deep tiles of 5..6 steps for radius 2 and 3 were built and measured: the
+// autotuner never chose them on 512^2..2048^2 grids (the halo of 2r rows per
+// level costs more than the passes saved).
+constexpr int max_deep_steps(int r) { return r == 1 ? 10 : 4; }
+
 // Builds a 3-D tiled tensor map over a float32 grid (nz, ny, nx) with the
 // given box; out-of-range box elements read as zero.  Returns false if the
 // grid cannot be described (row pitch or base not 16-byte aligned).

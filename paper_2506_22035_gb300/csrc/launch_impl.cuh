@@ -325,23 +325,24 @@ cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
   return v == 1 ? launch_fused_rh<MODE, R, 16, 1, 2>(T, ctx) : launch_fused_rh<MODE, R, 8, 1, 2>(T, ctx);
 }
 
-// Deep fusion for radius 1: T = 5..10 levels on a 16 x 64 output tile
-// (level 1 is 16 + 2(T-1) rows x 64 + 8(T-1) columns; one unit per warp on
-// the last levels).  For grids too small to fill the GPU a pass costs about
-// one tile's T levels, so fewer, deeper passes finish a run sooner although
-// the levels' halos repeat work.
-template <int T>
-using DeepTile = FuseCfg<1, T, 16, 64, 8, 8, 1, 2>;
+// Deep fusion (radius 1): T = 5..10 levels on a 16 x 64 output tile (level 1
+// is 16 + 2R(T-1) rows x 64 + 8(T-1) columns; one unit per warp on the last
+// levels).  For grids too small to fill the GPU a pass costs about one
+// tile's T levels, so fewer, deeper passes finish a run sooner although the
+// levels' halos repeat work.
+template <int R, int T>
+using DeepTile = FuseCfg<R, T, 16, 64, 8, 8, 1, 2>;
 
-template <Mode MODE>
+template <Mode MODE, int R>
 cudaError_t launch_fused_deep(int T, const LaunchCtx& ctx) {
+  if (T > max_deep_steps(R)) return cudaErrorNotSupported;
   switch (T) {
-    case 5: return launch_fused_cfg<DeepTile<5>, MODE>(ctx);
-    case 6: return launch_fused_cfg<DeepTile<6>, MODE>(ctx);
-    case 7: return launch_fused_cfg<DeepTile<7>, MODE>(ctx);
-    case 8: return launch_fused_cfg<DeepTile<8>, MODE>(ctx);
-    case 9: return launch_fused_cfg<DeepTile<9>, MODE>(ctx);
-    case 10: return launch_fused_cfg<DeepTile<10>, MODE>(ctx);
+    case 5: return launch_fused_cfg<DeepTile<R, 5>, MODE>(ctx);
+    case 6: return launch_fused_cfg<DeepTile<R, 6>, MODE>(ctx);
+    case 7: return launch_fused_cfg<DeepTile<R, 7>, MODE>(ctx);
+    case 8: return launch_fused_cfg<DeepTile<R, 8>, MODE>(ctx);
+    case 9: return launch_fused_cfg<DeepTile<R, 9>, MODE>(ctx);
+    case 10: return launch_fused_cfg<DeepTile<R, 10>, MODE>(ctx);
     default: return cudaErrorNotSupported;
   }
 }

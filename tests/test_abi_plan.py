@@ -309,7 +309,7 @@ def test_steps_per_pass_where_fusion_is_built(lib):
                     p.set_steps_per_pass(T)
                 assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
         with pytest.raises(spider.SpiderError):
-            p.set_steps_per_pass(5)
+            p.set_steps_per_pass(5)  # deep tiles (5..10) are built for radius 1
         p.close()
     p = plan(3, 1)
     p.set_engine("dense_tc")

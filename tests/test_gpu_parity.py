@@ -420,9 +420,14 @@ def test_deep_fusion_limits():
     p.close()
     w2 = si.normalised_coeffs(2, 2, "star", si.rng(24, 1))
     p2 = spider.Plan(w2, (64, 64), "star", "tf32")
+    p2.set_steps_per_pass(4)
     with pytest.raises(spider.SpiderError):
         p2.set_steps_per_pass(5)  # deep tiles are built for radius 1 only
     p2.close()
+    p3 = spider.Plan(w, (64, 64), "star", "f16x2")
+    with pytest.raises(spider.SpiderError):
+        p3.set_steps_per_pass(5)  # and for sparse TF32 only
+    p3.close()
 
 
 @pytest.mark.parametrize("T", [2, 3, 4])
