@@ -117,6 +117,9 @@ spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pas
  * boxes; 2 = 8 rows, one box, registers capped so three CTAs share an SM;
  * 3 = 16 rows, one box; 4 = small tiles (level 1 of 32 rows instead of 64,
  * one warp unit per warp per level) for grids that do not fill the GPU.
+ * FP16/BF16 splits and the dense engine: 2 and 3 = 8 rows with registers
+ * capped so two CTAs share an SM, two or one input boxes; CUDA-core engine:
+ * 2 and 3 run as 0 and 1.
  * 3-D: 0 and 4 = column blocks of 16 level-1 rows, warp units of 4 rows; 1
  * and 3 = 32 rows, units of 8; 2 = as 0 with registers capped for three CTAs
  * per SM at 2 steps per pass.  Any other value returns SPIDER_ERR_INVALID.

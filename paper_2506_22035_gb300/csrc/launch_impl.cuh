@@ -307,20 +307,27 @@ cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
   }
 }
 
-// Variants 2 and 3 exist for the TF32 sparse mode only (the split and dense
-// modes need more registers than variant 2 allows); elsewhere they run as
-// variants 0 and 1.  Variant 4 is the small tile: level 1 of 32 rows, one
-// warp unit per warp per level, four times the tiles of the 64-row shapes --
-// for grids too small to fill the GPU, where a pass is the latency of one
-// tile's levels.
+// Variants 2 and 3 differ by mode.  Sparse TF32: 2 = H 8 with registers
+// capped for three CTAs per SM, 3 = H 16 with one input box.  FP16/BF16
+// splits and dense TF32 (150..190 registers uncapped, one CTA per SM):
+// 2 and 3 = H 8 with registers capped for two CTAs per SM, two or one input
+// boxes (124..128 registers, at most a few spilled words).  CUDA cores (W
+// in registers): 2 and 3 run as 0 and 1.  Variant 4 is the small tile: level
+// 1 of 32 rows, one warp unit per warp per level, four times the tiles of
+// the 64-row shapes -- for grids too small to fill the GPU, where a pass is
+// the latency of one tile's levels.
 template <Mode MODE, int R>
 cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
   int v = ctx.plan->tile_variant;
   if (v == 4) return launch_fused_rh<MODE, R, 8, 1, 2, 32>(T, ctx);
-  if (MODE != Mode::SpTF32 && v >= 2) v -= 2;
   if constexpr (MODE == Mode::SpTF32) {
     if (v == 2) return launch_fused_rh<MODE, R, 8, 3, 1>(T, ctx);
     if (v == 3) return launch_fused_rh<MODE, R, 16, 1, 1>(T, ctx);
+  } else if constexpr (MODE != Mode::CudaCore) {
+    if (v == 2) return launch_fused_rh<MODE, R, 8, 2, 2>(T, ctx);
+    if (v == 3) return launch_fused_rh<MODE, R, 8, 2, 1>(T, ctx);
+  } else {
+    if (v >= 2) v -= 2;
   }
   return v == 1 ? launch_fused_rh<MODE, R, 16, 1, 2>(T, ctx) : launch_fused_rh<MODE, R, 8, 1, 2>(T, ctx);
 }
