@@ -212,9 +212,11 @@ void spider_plan_destroy(spider_plan plan);
  * claimed from a device queue in step-major order, and step s of a tile
  * starts only after the tile and its eight neighbours finished step s-1
  * (per-tile counters, bounded waits).  Such grids of at least 2^21 points
- * and more than one step run first, through spider_run with fused passes
- * (the plan's steps per pass if above 1, else the autotuned choice of its
- * kind of stencil, else 2).  Other plans (3-D, split precisions, comparator
+ * and more than one step run through spider_run with fused passes instead
+ * (the plan's steps per pass and tile variant if it fuses, else the
+ * autotuned choice of its kind of stencil, else 2 steps on variant 2), on
+ * library-owned side streams concurrently with the persistent launch (they
+ * start after the work already queued on `stream`).  Other plans (3-D, split precisions, comparator
  * engines, radius above 3) run through spider_run on the same stream after
  * the persistent launch.  Grids whose rows are not a multiple of 4 floats,
  * or whose buffers are not 16-byte aligned, use the plan's padded grids (see

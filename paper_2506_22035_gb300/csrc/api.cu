@@ -242,7 +242,7 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
 // the plan's device state is.
 constexpr size_t kMaxRunGraphs = 8;
 
-static spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
+spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (steps < 1 || cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();

@@ -34,6 +34,45 @@ constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
 constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
 constexpr int kMaxTableSmem = 48 * 1024;
 constexpr long long kFuseMinPoints = 1LL << 21;  // grids this large run as fused passes of their own
+constexpr int kSideStreams = 8;                  // streams the fused grids run on, next to the queue
+
+// Non-blocking streams for the grids that run as fused passes beside the
+// persistent queue, kept per device for the process.
+cudaStream_t side_stream(int dev, int k) {
+  static std::mutex mu;
+  static cudaStream_t pool[64][kSideStreams] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!pool[dev][k] && cudaStreamCreateWithFlags(&pool[dev][k], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    pool[dev][k] = nullptr;
+  }
+  return pool[dev][k];
+}
+
+// Orders `stream` after the work issued on the side streams (on every way
+// out of spider_batch, so a caller's later work on `stream` sees the grids).
+struct SideJoin {
+  cudaStream_t stream = nullptr;
+  cudaStream_t sides[kSideStreams] = {};
+  bool used = false;
+  void join() {
+    if (!used) return;
+    used = false;
+    for (cudaStream_t s : sides) {
+      if (!s) continue;
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamSynchronize(s);  // no event: wait on the host instead
+        continue;
+      }
+      cudaEventRecord(ev, s);
+      cudaStreamWaitEvent(stream, ev, 0);
+      cudaEventDestroy(ev);
+    }
+  }
+  ~SideJoin() { join(); }
+};
 
 // Step s reads `in` (s = 0) or bufs[(first + s - 1) % 2] and writes `out`
 // (the last step) or bufs[(first + s) % 2].  When in, out and the plan's
@@ -371,10 +410,11 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
   }
   // Jobs the persistent queue handles: 2-D sparse TF32, radius <= 3, at
   // least one step, and fewer than kFuseMinPoints points.  Larger grids of
-  // several steps run first, as fused multi-step passes of their own (the
-  // plan's tuned depth, else the tuned depth of its kind, else 2 steps per
-  // pass): the queue takes one step per HBM pass.  The rest run through
-  // their own plan after the persistent launch.
+  // several steps run as fused multi-step passes of their own (the plan's
+  // tuned depth and tile, else those of its kind, else 2 steps per pass on
+  // tile variant 2), on side streams beside the queue: the queue takes one
+  // step per HBM pass.  The rest run through their own plan after the
+  // persistent launch.
   std::vector<int> queued, fused, direct;
   for (int i = 0; i < n; ++i) {
     spider_plan_t* p = plans[i];
@@ -383,21 +423,44 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     const bool big = ok && steps[i] > 1 && p->points() >= kFuseMinPoints;
     (big ? fused : ok ? queued : direct).push_back(i);
   }
-  for (int i : fused) {
-    spider_plan_t* p = plans[i];
-    std::lock_guard<std::mutex> lock(p->mu);
-    const int old_T = p->steps_per_pass, old_v = p->tile_variant;
-    int T = old_T, v = old_v;
-    if (T < 2 && !autotune_lookup(p, &T, &v)) {
-      T = 2;
-      v = 0;
+  // The fused grids run on side streams (after the work already on
+  // `stream`), concurrently with each other and with the queue: a pass over
+  // a grid of a few million points is a few microseconds, so one after
+  // another they would be bound by launch latency.  Repeated calls with the
+  // same grids replay each job's passes as a CUDA graph.
+  SideJoin side;
+  side.stream = stream;
+  if (!fused.empty()) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess)
+      return fail(SPIDER_ERR_CUDA, "batch event");
+    cudaEventRecord(start, stream);
+    for (int k = 0; k < kSideStreams; ++k) {
+      side.sides[k] = side_stream(dev, k);
+      if (side.sides[k]) cudaStreamWaitEvent(side.sides[k], start, 0);
     }
-    p->steps_per_pass = T;
-    p->tile_variant = v;
-    spider_status s = run_device(p, ins[i], outs[i], steps[i], stream);
-    p->steps_per_pass = old_T;
-    p->tile_variant = old_v;
-    if (s != SPIDER_OK) return s;
+    cudaEventDestroy(start);
+    side.used = true;
+    for (size_t n = 0; n < fused.size(); ++n) {
+      const int i = fused[n];
+      cudaStream_t s_run = side.sides[n % kSideStreams] ? side.sides[n % kSideStreams] : stream;
+      spider_plan_t* p = plans[i];
+      std::lock_guard<std::mutex> lock(p->mu);
+      const int old_T = p->steps_per_pass, old_v = p->tile_variant;
+      int T = old_T, v = old_v;
+      if (T < 2 && !autotune_lookup(p, &T, &v)) {
+        T = 2;
+        v = 2;  // measured best untuned choice on the mixed batch (v 0: 805, v 2: 847, v 4: 777 GStencil/s)
+      }
+      p->steps_per_pass = T;
+      p->tile_variant = v;
+      spider_status s = run_cached(p, ins[i], outs[i], steps[i], s_run);
+      p->steps_per_pass = old_T;
+      p->tile_variant = old_v;
+      if (s != SPIDER_OK) return s;
+    }
   }
   if (!queued.empty()) {
     const int nq = (int)queued.size();
@@ -570,6 +633,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, stream);
+    side.join();  // the fused grids ran beside the queue; the wait below covers them
     int status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, a_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -578,10 +642,13 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
     if (status != 0) return fail(SPIDER_ERR_TIMEOUT, "a dependency wait in the batch queue ran out");
   }
+  side.join();
   for (int i : direct) {
     std::lock_guard<std::mutex> lock(plans[i]->mu);
     spider_status s = run_device(plans[i], ins[i], outs[i], steps[i], stream);
     if (s != SPIDER_OK) return s;
   }
+  const cudaError_t e = cudaStreamSynchronize(stream);  // synchronous: every grid is done
+  if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
   return SPIDER_OK;
 }
