@@ -25,6 +25,11 @@
 #include "stencil_kernels.cuh"
 
 namespace spider {
+
+// api.cu: run_device, with repeated (grids, steps, configuration) calls
+// captured once and replayed as a CUDA graph (plan lock held by the caller).
+spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
+
 namespace {
 
 constexpr int kBY = 64, kBX = 128, kWarpsY = 4, kWarpsX = 2, kH = 16;

@@ -131,9 +131,6 @@ int combos_per_plane(spider_precision prec, int ry);
 
 // api.cu: enqueue `steps` steps in -> out on `stream` (plan lock held by the caller).
 spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
-// api.cu: run_device, with repeated (grids, steps, configuration) calls
-// captured once and replayed as a CUDA graph (plan lock held by the caller).
-spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t steps, cudaStream_t stream);
 // api.cu: the largest number of time steps per HBM pass built for the plan
 // (fused kernels: 2-D stencils, and 3-D radius-1 stencils in sparse TF32).
 int max_steps_per_pass(const spider_plan_t* p);
