@@ -94,6 +94,27 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     p3.close()
 
 
+def test_batch_rejects_bad_arguments_without_touching_a_device(lib):
+    # every case fails in the argument checks, before any device call
+    a = spider.Plan(np.ones((3, 3), np.float32), (8, 8))
+    b = spider.Plan(np.ones((3, 3), np.float32), (8, 8))
+    P = lambda *h: (ctypes.c_void_p * len(h))(*h)
+    S = lambda *n: (ctypes.c_int64 * len(n))(*n)
+    ok_in, ok_out = P(4096, 1 << 20), P(1 << 21, 1 << 22)
+    assert lib.spider_batch(-1, P(a.handle), P(4096), P(1 << 20), S(1), None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch(5000, P(a.handle), P(4096), P(1 << 20), S(1), None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch(0, None, None, None, None, None) == _native.SPIDER_OK      # nothing to do
+    assert lib.spider_batch(1, None, P(4096), P(1 << 20), S(1), None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch(1, P(a.handle), P(4096), P(1 << 20), S(-1), None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch(1, P(a.handle), P(4096), P(4096 + 16), S(1), None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch(1, P(None), P(4096), P(1 << 20), S(1), None) == _native.SPIDER_ERR_INVALID
+    # a plan owns its scratch grids: it may appear once per batch
+    assert lib.spider_batch(2, P(a.handle, a.handle), ok_in, ok_out, S(1, 1), None) == _native.SPIDER_ERR_INVALID
+    assert "once" in lib.spider_last_error().decode()
+    a.close()
+    b.close()
+
+
 # ------------------------------------------------------------------ operand decoding
 # Decoding uses the fragment maps of the sparse TF32 m16n8k16 MMA (measured on
 # the device): A compressed 16 x 8 with a0 (g, q), a1 (g+8, q), a2 (g, q+4),
