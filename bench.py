@@ -527,7 +527,9 @@ def run_batched(a):
             "data": "synthetic",
             "config": {"workload": "batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, "
                                    "10-200 steps", "stencil_updates_per_step": work, "engine": "sparse_tc",
-                       "launch": "spider_batch (persistent tile queue, CUDA graph)"},
+                       "launch": "one spider_batch call: grids of >= 2^16 points as fused passes on side streams, "
+                                 "each replayed as a CUDA graph; smaller grids and single steps in the persistent "
+                                 "tile queue (one graph launch)"},
             "sequential_spider_run": {"value": work / dt_seq / 1e9, "unit": "GStencil/s",
                                       "note": "same jobs, one autotuned spider_run after another"}}
     for p in plans:

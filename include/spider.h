@@ -211,7 +211,7 @@ void spider_plan_destroy(spider_plan plan);
  * issued as a CUDA graph: work items (time step, grid, 64 x 128 tile) are
  * claimed from a device queue in step-major order, and step s of a tile
  * starts only after the tile and its eight neighbours finished step s-1
- * (per-tile counters, bounded waits).  Such grids of at least 2^21 points
+ * (per-tile counters, bounded waits).  Such grids of at least 2^16 points
  * and more than one step run through spider_run with fused passes instead
  * (the plan's steps per pass and tile variant if it fuses, else the
  * autotuned choice of its kind of stencil, else 2 steps on variant 2), on

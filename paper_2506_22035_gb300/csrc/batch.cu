@@ -38,7 +38,15 @@ constexpr int kMaxStageFloats = (kBY + 2 * kMaxR) * (kBX + 2 * kHaloX);
 constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
 constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
 constexpr int kMaxTableSmem = 48 * 1024;
-constexpr long long kFuseMinPoints = 1LL << 21;  // grids this large run as fused passes of their own
+// Grids of at least this many points (with more than one step) run as fused
+// passes of their own on side streams; smaller ones, and single steps, go
+// through the persistent queue.  Measured on the mixed batch of 64 grids of
+// 256^2..4096^2 (GStencil/s, replayed): threshold 2^21: 867, 2^19: 1000,
+// 2^18: 1014, 2^16 (every grid of the mix fused): 1114 -- a queue item
+// carries one step and each step of a job waits for the previous one, so a
+// small job with many steps is a chain of queue latencies, where its fused
+// passes replayed as a graph take two steps per few-microsecond launch.
+constexpr long long kFuseMinPoints = 1LL << 16;
 constexpr int kSideStreams = 8;                  // streams the fused grids run on, next to the queue
 
 // Non-blocking streams for the grids that run as fused passes beside the
@@ -598,9 +606,14 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     if (attr_err != cudaSuccess) return fail(SPIDER_ERR_CUDA, "batch kernel attributes");
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads + 64, smem_bytes);
+    // No more CTAs than the largest step has tiles: the items of a step wait
+    // for the previous step, so further CTAs would only hold SMs (and their
+    // shared memory) that the fused passes on the side streams can use.
     const long long total_items = step_off[max_steps];
+    long long widest_step = 1;
+    for (int s = 0; s < max_steps; ++s) widest_step = std::max(widest_step, step_off[s + 1] - step_off[s]);
     const int grid = (int)std::max<long long>(
-        1, std::min<long long>(total_items, (long long)std::max(occ, 1) * device_sm_count()));
+        1, std::min({total_items, widest_step, (long long)std::max(occ, 1) * device_sm_count()}));
     // The persistent launch is issued as a CUDA graph: the work-queue reset
     // (counter and per-tile step counters) and the kernel, launched on the
     // caller's stream.

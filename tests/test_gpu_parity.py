@@ -465,16 +465,18 @@ def test_autotune_keeps_results_within_tolerance():
 def _batch_jobs():
     jobs = []
     g = np.random.default_rng(77)
-    # the second last grid is just under 2^21 points (many tiles per step in
-    # the queue); the last one is larger and runs as fused passes of its own
+    # grids under 2^16 points and single-step jobs go through the persistent
+    # queue (the four 200 x 320 grids give it about 50 tiles per step, the
+    # 300 x 520 one-step job 15 at once); the others run as fused passes of
+    # their own on side streams
     shapes = [(300, 520), (64, 128), (1, 512), (257, 1000), (90, 132), (70, 130), (128, 256), (33, 64),
-              (1400, 1400), (1100, 2000)]
+              (1400, 1400), (1100, 2000), (200, 320), (200, 320), (200, 320), (200, 320)]
     for i, ext in enumerate(shapes):
         r = 1 + i % 3
         kind = "box" if i % 2 == 0 else "star"
         u0 = g.uniform(0, 1, ext).astype(np.float32)
         w = si.normalised_coeffs(2, r, kind, g)
-        steps = [1, 7, 12, 3, 20, 2, 9, 5, 7, 4][i]
+        steps = [1, 7, 12, 3, 20, 2, 9, 5, 7, 4, 6, 9, 11, 14][i]
         jobs.append((u0, w, kind, steps))
     return jobs
 
