@@ -6,7 +6,7 @@ step of it (e.g. 100 steps of a 7x7 box stencil on an 8192^2 grid), with the
 input grid resident in HBM.  GStencil/s = grid points x time steps / seconds
 / 1e9.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d|batched|serving|sweep]
+  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d|batched|batched_small|serving|sweep]
                   [--precision tf32|f16x2|bf16x3] [--impl spider|reference] [--accuracy]
 
 Under torchrun every rank runs the whole workload on its own GPU (independent
@@ -40,7 +40,8 @@ WORKLOADS = {
     "heat3d": si.HEAT3D_512,
     "box3d": si.BOX3D_512,
 }
-DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60, "batched": 10, "serving": 40}
+DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60, "batched": 10, "batched_small": 10,
+                 "serving": 40}
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 
@@ -51,7 +52,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spider", choices=["spider", "reference"])
-    ap.add_argument("--workload", default="box2d", choices=sorted(WORKLOADS) + ["batched", "serving", "sweep"])
+    ap.add_argument("--workload", default="box2d",
+                    choices=sorted(WORKLOADS) + ["batched", "batched_small", "serving", "sweep"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
     ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
@@ -493,7 +495,9 @@ def run_batched(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    jobs = si.batched_jobs()[: a.jobs] if a.jobs else si.batched_jobs()
+    small = a.workload == "batched_small"
+    all_jobs = si.batched_small_jobs() if small else si.batched_jobs()
+    jobs = all_jobs[: a.jobs] if a.jobs else all_jobs
     plans, ins, outs = [], [], []
     work = 0
     for jb in jobs:
@@ -525,8 +529,11 @@ def run_batched(a):
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
             "data": "synthetic",
-            "config": {"workload": "batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, "
-                                   "10-200 steps", "stencil_updates_per_step": work, "engine": "sparse_tc",
+            "config": {"workload": ("batched_small: 256 2-D grids, sides log-uniform [32, 255] (< 2^16 points "
+                                    "each), star/box r 1-3, 10-200 steps") if small else
+                                   ("batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, "
+                                    "10-200 steps"),
+                       "stencil_updates_per_step": work, "engine": "sparse_tc",
                        "launch": "one spider_batch call: grids of >= 2^16 points as fused passes on side streams, "
                                  "each replayed as a CUDA graph; smaller grids and single steps in the persistent "
                                  "tile queue (one graph launch)"},
@@ -660,7 +667,7 @@ def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.workload == "batched":
+    if a.workload in ("batched", "batched_small"):
         return run_batched(a)
     if a.workload == "serving":
         return run_serving(a)

@@ -131,6 +131,23 @@ def batched_jobs(n: int = 64, workload: int = 3) -> list[Job]:
     return jobs
 
 
+def batched_small_jobs(n: int = 256, workload: int = 5) -> list[Job]:
+    """Small-grid batch: 2-D grids, each side log-uniform in [32, 255] (drawn
+    independently per axis, so every grid has fewer than 2^16 points), shape
+    uniform in {star, box}, r uniform in {1, 2, 3}, steps uniform in
+    [10, 200]."""
+    g = rng(workload, 0)
+    jobs = []
+    for i in range(n):
+        ny = log_uniform_int(g, 32, 255)
+        nx = log_uniform_int(g, 32, 255)
+        shape = STAR if g.integers(0, 2) == 0 else BOX
+        r = int(g.integers(1, 4))
+        steps = int(g.integers(10, 201))
+        jobs.append(Job(2, (ny, nx), shape, r, steps, BASE_SEED + workload + 7919 * (i + 1)))
+    return jobs
+
+
 def serving_arrivals(n: int = 2000, rate_per_s: float = 200.0, workload: int = 4) -> list[Job]:
     """Serving mix: Poisson arrivals; half 2-D (side log-uniform 256-8192),
     half 3-D (side log-uniform 64-512); r uniform 1..3; shape uniform
