@@ -1,16 +1,19 @@
 // spider_batch: many 2-D grids of different sizes, radii and step counts in
-// one persistent launch over a device work queue.
+// one call.  Small grids (and single steps) share one persistent launch over
+// a device work queue; larger grids run as fused multi-step passes of their
+// own on side streams beside it (see kFuseMinPoints).
 //
-// Work items are (time step s, job, tile) in step-major order; CTAs claim them
-// with one atomic counter.  Item (s, j, tile) reads job j's grid of step s
-// over the tile plus its halo, so it may start only after the tile and its
-// eight neighbours have finished step s-1 (those are also the last readers of
-// the buffer it overwrites).  Each job keeps one completion counter per tile;
-// a CTA waits on its neighbours' counters with bounded spins (acquire loads)
-// and publishes its own with a release store after a device-scope fence.
-// Because items are claimed in global order and an item only waits on items
-// of an earlier step, every awaited item is already held by a running CTA:
-// the queue cannot deadlock, whatever the residency.
+// Queue work items are (time step s, job, tile) in step-major order; CTAs
+// claim them with one atomic counter.  Item (s, j, tile) reads job j's grid
+// of step s over the tile plus its halo, so it may start only after the tile
+// and its eight neighbours have finished step s-1 (those are also the last
+// readers of the buffer it overwrites).  Each job keeps one completion counter
+// per tile; a producer warp waits on the neighbours' counters with bounded
+// spins (acquire loads) and publishes a tile's counter with a release store
+// once every consumer warp has handed the tile's stage back.  Because every
+// CTA claims and processes its items in global order and an item only waits
+// on items of an earlier step, every awaited item is already held by a
+// running CTA: the queue cannot deadlock, whatever the residency.
 //
 // The tile computation is the one-step SPIDER tile of stencil_step_kernel
 // (TF32 sparse MMA, 64 x 128 outputs, TMA halo box).  Each job brings its own
