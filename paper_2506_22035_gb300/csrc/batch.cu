@@ -443,8 +443,8 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
   }
   // The fused grids run on side streams (after the work already on
   // `stream`), concurrently with each other and with the queue: a pass over
-  // a grid of a few million points is a few microseconds, so one after
-  // another they would be bound by launch latency.  Repeated calls with the
+  // one of these grids lasts microseconds, so one after another they would
+  // be bound by launch latency.  Repeated calls with the
   // same grids replay each job's passes as a CUDA graph.
   SideJoin side;
   side.stream = stream;
@@ -461,9 +461,9 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     }
     cudaEventDestroy(start);
     side.used = true;
-    for (size_t n = 0; n < fused.size(); ++n) {
-      const int i = fused[n];
-      cudaStream_t s_run = side.sides[n % kSideStreams] ? side.sides[n % kSideStreams] : stream;
+    for (size_t f = 0; f < fused.size(); ++f) {
+      const int i = fused[f];
+      cudaStream_t s_run = side.sides[f % kSideStreams] ? side.sides[f % kSideStreams] : stream;
       spider_plan_t* p = plans[i];
       std::lock_guard<std::mutex> lock(p->mu);
       const int old_T = p->steps_per_pass, old_v = p->tile_variant;
