@@ -433,3 +433,16 @@ def test_wide_radius_limits(lib):
         with pytest.raises(spider.SpiderError) as e:
             create(nd, r, prec)
         assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
+
+
+def test_batched_workload_generators_match_their_descriptions():
+    # the small-grid batch must stay under the queue's 2^16-point routing
+    # threshold; the mix spans it (sides 256..4096); both are reproducible
+    import stencil_inputs as si
+    small, mix = si.batched_small_jobs(), si.batched_jobs()
+    assert len(small) == 256 and len(mix) == 64
+    assert all(32 <= s <= 255 for j in small for s in j.extents)
+    assert max(int(np.prod(j.extents)) for j in small) < 2 ** 16
+    assert all(256 <= s <= 4096 for j in mix for s in j.extents)
+    assert all(10 <= j.steps <= 200 and 1 <= j.r <= 3 for j in small + mix)
+    assert si.batched_small_jobs() == small and si.batched_jobs() == mix
