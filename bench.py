@@ -6,8 +6,9 @@ step of it (e.g. 100 steps of a 7x7 box stencil on an 8192^2 grid), with the
 input grid resident in HBM.  GStencil/s = grid points x time steps / seconds
 / 1e9.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload box2d|heat2d|heat3d|box3d|batched|batched_small|serving|sweep]
-                  [--precision tf32|f16x2|bf16x3] [--impl spider|reference] [--accuracy]
+  python bench.py [--gpus N --steps K --warmup W]
+                  [--workload box2d|heat2d|heat3d|box3d|batched|batched_small|serving|sweep|mma_peak]
+                  [--precision tf32|f16x2|bf16x3] [--impl spider|reference] [--no-accuracy] [--no-workloads]
 
 Under torchrun every rank runs the whole workload on its own GPU (independent
 replicas, weak scaling); the reported value is the total over ranks divided
@@ -41,7 +42,7 @@ WORKLOADS = {
     "box3d": si.BOX3D_512,
 }
 DEFAULT_STEPS = {"box2d": 300, "heat2d": 2000, "heat3d": 60, "box3d": 60, "batched": 10, "batched_small": 10,
-                 "serving": 40}
+                 "serving": 1, "sweep": 10, "mma_peak": 1}
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 
@@ -53,7 +54,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spider", choices=["spider", "reference"])
     ap.add_argument("--workload", default="box2d",
-                    choices=sorted(WORKLOADS) + ["batched", "batched_small", "serving", "sweep"])
+                    choices=sorted(WORKLOADS) + ["batched", "batched_small", "serving", "sweep", "mma_peak"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
     ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
@@ -67,8 +68,14 @@ def parse_args():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--accuracy", action="store_true",
-                    help="also compute the full-size relative L2 error against the FP64 oracle")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the full-grid relative L2 error against the FP64 oracle (computed by default)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other configurations (Heat-2D, Heat-3D, Box-3D, batched, serving) in the "
+                         "default line")
+    ap.add_argument("--serving-jobs", type=int, default=None,
+                    help="serving: how many of the 2000 Poisson arrivals to run (default 600; 200 in the "
+                         "default line's summary)")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = DEFAULT_STEPS[a.workload]
@@ -439,7 +446,7 @@ def run_spider(a):
     if rank == 0 and not a.no_comparators:
         comps = {}
         variants = [("sparse_tc", "tf32"), ("sparse_tc", "f16x2"), ("sparse_tc", "bf16x3"), ("dense_tc", "tf32"),
-                    ("cuda_core", "tf32")]
+                    ("cuda_core", "tf32"), ("sparse_tc_copy", "tf32")]
         for eng, prec in variants:
             if (eng, prec) == (a.engine, a.precision):
                 continue
@@ -460,17 +467,41 @@ def run_spider(a):
             p2.close()
         result["comparators"] = comps
 
-    if rank == 0 and a.accuracy:
+    if rank == 0 and not a.no_accuracy:
+        # full-grid relative L2 error of every precision against the FP64
+        # oracle (outside the timed region), each at its autotuned setting
         import oracle
-        ref = oracle.stencil(u0, w, wl.steps)
-        ref_t = torch.from_numpy(ref).to(dev)
+        ref_t = torch.from_numpy(oracle.stencil(u0, w, wl.steps)).to(dev)
         errs = {}
         for prec in ("tf32", "f16x2", "bf16x3"):
-            p2 = spider.Plan(w, wl.extents, wl.shape, prec)
+            p2 = spider.Plan(w, wl.extents, wl.shape, prec, a.engine)
+            if prec == a.precision:
+                p2.set_steps_per_pass(a.steps_per_pass)
+                p2.set_tile_variant(a.tile_variant)
+            else:
+                p2.autotune(a_in, b_out, wl.steps, stream)
             p2.run(a_in, b_out, wl.steps, stream)
-            errs[prec] = spider.relative_l2_error(b_out, ref_t, stream)
+            errs[prec] = {"rel_l2": spider.relative_l2_error(b_out, ref_t, stream),
+                          "a_priori_bound": p2.error_bound(wl.steps)}
             p2.close()
+        del ref_t
         result["rel_l2_error_vs_fp64"] = errs
+
+    if rank == 0 and a.workload == "box2d" and a.radius in (None, 3) and not a.extents:
+        # the tensor-pipe roofline of the fused kernel: sparse MMAs per launch
+        # (its tile geometry) over the measured mma.sp peak of this GPU
+        peak_mma = spider.measure_mma_rate("sp_tf32" if a.precision == "tf32" else "sp_f16", stream)
+        mmas = fused_mmas_per_launch(wl.extents, wl.r, a.steps_per_pass, a.tile_variant)
+        if mmas is not None and a.precision == "tf32" and a.engine == "sparse_tc":
+            achieved = mmas / per_launch_s
+            result["roofline_tensor"] = {
+                "bound": "tensor", "achieved": achieved / 1e9, "peak": peak_mma / 1e9, "unit": "G mma.sp/s",
+                "frac": achieved / peak_mma, "mmas_per_launch": mmas,
+                "peak_source": "measured: spider_measure_mma_rate (mma.sp m16n8k16 TF32, operands in registers)"}
+
+    if rank == 0 and world == 1 and not a.no_workloads and a.workload == "box2d" and not a.extents \
+            and a.radius in (None, 3):
+        result["workloads"] = other_workloads(a, spider, dev, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(wl)
@@ -481,6 +512,124 @@ def run_spider(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fused_mmas_per_launch(extents, r, T, variant):
+    """Sparse MMAs one launch of the fused 2-D TF32 kernel issues: every tile
+    computes levels 1..T, level t of BY + 2r(T - t) rows and BX + 8(T - t)
+    columns in warp units of H rows x 64 columns, each unit (H / 2)(2r + 2)
+    MMAs (level 1 is 64 rows, 32 for variant 4; BY = level 1 - 2r(T - 1),
+    BX = 8(17 - T); H = 16 for variants 1 and 3, else 8).  Deep tiles (T > 4)
+    are 16 x 64 outputs.  None for T = 1 (the one-step kernel)."""
+    if T < 2:
+        return None
+    ny, nx = extents
+    if T > 4:
+        by, bx, h = 16, 64, 8
+    else:
+        l1 = 32 if variant == 4 else 64
+        by, bx, h = l1 - 2 * r * (T - 1), 8 * (17 - T), 16 if variant in (1, 3) else 8
+    units = 0
+    for t in range(1, T + 1):
+        rows, cols = by + 2 * r * (T - t), bx + 8 * (T - t)
+        units += -(-rows // h) * -(-(cols // 8) // 8)
+    tiles = -(-nx // bx) * -(-ny // by)
+    return tiles * units * (h // 2) * (2 * r + 2)
+
+
+def timed_workload(spider, wl, dev, stream, runs=5, with_error=True, tune=True):
+    """GStencil/s, steps per pass, HBM roofline and error vs FP64 of one
+    workload run through spider_run (sparse TF32, autotuned)."""
+    import torch
+    u0, w = si.workload_inputs(wl)
+    pts = int(np.prod(wl.extents))
+    plan = spider.Plan(w, wl.extents, wl.shape, "tf32")
+    x = torch.from_numpy(u0).to(dev)
+    y = torch.empty_like(x)
+    T, v = plan.autotune(x, y, wl.steps, stream) if tune else (1, 0)
+    flush = None if 4 * pts > L2_BYTES else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        plan.run(x, y, wl.steps, stream)
+    dt = time_runs(plan, x, y, wl.steps, runs, flush, stream)
+    plan.sync(stream)
+    launches = runs * (wl.steps // T + (1 if wl.steps % T else 0))
+    per_launch = dt / launches
+    peaks, kind = measured_peaks()
+    hbm = 8.0 * pts / per_launch / 1e9
+    rec = {"workload": f"{wl.name}, {wl.steps} time steps", "gstencil_s": pts * wl.steps * runs / dt / 1e9,
+           "us_per_run": dt / runs * 1e6, "steps_per_pass": T, "tile_variant": v,
+           "roofline": {"bound": "hbm", "achieved": hbm, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                        "frac": hbm / float(peaks["hbm_gbs"]), "peak_source": f"{kind} HBM copy bandwidth"}}
+    if with_error:
+        import oracle
+        ref = torch.from_numpy(oracle.stencil(u0, w, wl.steps)).to(dev)
+        plan.run(x, y, wl.steps, stream)
+        rec["rel_l2_error_vs_fp64"] = spider.relative_l2_error(y, ref, stream)
+        rec["a_priori_bound"] = plan.error_bound(wl.steps)
+        del ref
+    plan.close()
+    return rec, (u0, w, T, v)
+
+
+def other_workloads(a, spider, dev, stream):
+    """The configurations besides the headline, measured in the same process:
+    Heat-2D 512^2 (latency-bound: its time against the same passes on a
+    one-tile grid), Heat-3D and Box-3D 512^3 (HBM roofline), the batched mix
+    (one spider_batch call) and a serving summary."""
+    import torch
+    out = {}
+    rec, (u0, w, T, v) = timed_workload(spider, si.HEAT2D_512, dev, stream, runs=50)
+    # latency floor: the same passes on a grid of one 16 x 64 tile (the
+    # critical path of one tile's levels per pass, plus the launches)
+    one = spider.Plan(w, (16, 64), "star", "tf32")
+    if T > 1:
+        one.set_steps_per_pass(T)
+    one.set_tile_variant(v)
+    x1 = torch.from_numpy(np.ascontiguousarray(u0[:16, :64])).to(dev)
+    y1 = torch.empty_like(x1)
+    for _ in range(5):
+        one.run(x1, y1, si.HEAT2D_512.steps, stream)
+    floor = time_runs(one, x1, y1, si.HEAT2D_512.steps, 50, None, stream) / 50
+    one.close()
+    rec["roofline"] = {"bound": "latency", "achieved_us": rec["us_per_run"], "floor_us": floor * 1e6,
+                       "frac": floor * 1e6 / rec["us_per_run"],
+                       "floor": "the same passes (steps per pass, tile variant, graph replay) on a one-tile "
+                                "16 x 64 grid: per pass the chain of one tile's levels plus the launch",
+                       "l2_gbs": 8.0 * 512 * 512 * (-(-si.HEAT2D_512.steps // T)) / (rec["us_per_run"] * 1e-6) / 1e9}
+    out["heat2d"] = rec
+    out["heat3d"] = timed_workload(spider, si.HEAT3D_512, dev, stream)[0]
+    out["box3d"] = timed_workload(spider, si.BOX3D_512, dev, stream)[0]
+    out["batched"] = batched_summary(spider, dev, stream, calls=5)
+    out["serving"] = serving_run(spider, n_jobs=a.serving_jobs or 200)
+    return out
+
+
+def batched_summary(spider, dev, stream, calls=5):
+    """One spider_batch call over the 64-grid mix: GStencil/s over `calls`
+    timed calls after three warm-up calls (graphs captured and replayed)."""
+    import torch
+    jobs = si.batched_jobs()
+    plans, ins, outs, work = [], [], [], 0
+    for jb in jobs:
+        u0, w = si.job_inputs(jb)
+        plans.append(spider.Plan(w, jb.extents, jb.shape, "tf32"))
+        ins.append(torch.from_numpy(u0).to(dev))
+        outs.append(torch.empty_like(ins[-1]))
+        work += int(np.prod(jb.extents)) * jb.steps
+    steps = [jb.steps for jb in jobs]
+    for _ in range(3):
+        spider.batch(plans, ins, outs, steps, stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        spider.batch(plans, ins, outs, steps, stream)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    for p in plans:
+        p.close()
+    return {"workload": "batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, 10-200 steps",
+            "gstencil_s": work * calls / dt / 1e9, "ms_per_call": dt / calls * 1e3, "stencil_updates": work,
+            "timing": "host clock around synchronous spider_batch calls"}
 
 
 def run_batched(a):
@@ -604,62 +753,92 @@ def run_sweep(a):
     return 0
 
 
+def serving_run(spider, n_jobs=600, budget=120 * 10**9):
+    """The serving configuration: the first `n_jobs` of the 2000 Poisson
+    arrivals (200 jobs/s; 2-D sides 256-8192, 3-D sides 64-512, r 1-3, 10-500
+    steps, error target 1e-3 or 1e-5) submitted at their arrival times to a
+    server with a 120 GB HBM budget; jobs are neither capped nor
+    time-compressed.  Latency is each job's submit-to-completion time."""
+    jobs = si.serving_arrivals()[:n_jobs]
+    pool = si.serving_grid_pool(jobs)
+    work = [int(np.prod(j.extents)) * j.steps for j in jobs]
+    server = spider.Server(budget)
+    plans = [spider.Plan(si.serving_job_coeffs(j), j.extents, j.shape, "tf32") for j in jobs]
+    pending, lat, done_at = {}, [], []
+    t0 = time.perf_counter()
+    base = jobs[0].arrival_s
+
+    def drain():
+        for t in list(pending):
+            done, _ = server.poll(t)
+            if done:
+                out = np.empty(pending.pop(t), np.float32)
+                _, l = server.poll(t, out)   # copies the result and releases the ticket
+                lat.append(l)
+                done_at.append(time.perf_counter() - t0)
+
+    for j, p in zip(jobs, plans):
+        while time.perf_counter() - t0 < j.arrival_s - base:
+            drain()
+            time.sleep(0.0002)
+        n = int(np.prod(j.extents))
+        pending[server.submit(p, pool[:n].reshape(j.extents), j.steps, j.err_target)] = n
+    while pending:
+        drain()
+        time.sleep(0.0005)
+    server.close()
+    for p in plans:
+        p.close()
+    ls = np.sort(np.asarray(lat))
+    span = jobs[-1].arrival_s - base
+    busy = max(done_at)
+    return {"workload": f"serving: first {len(jobs)} of 2000 Poisson arrivals at 200 jobs/s, 2-D side 256-8192 / "
+                        "3-D side 64-512, r 1-3, 10-500 steps, error target 1e-3 or 1e-5, 120 GB HBM budget",
+            "jobs_completed": len(lat), "stencil_updates": int(sum(work)),
+            "latency_s": {"p50": float(np.percentile(ls, 50)), "p99": float(np.percentile(ls, 99)),
+                          "max": float(ls[-1])},
+            "offered_gstencil_s": sum(work) / max(span, 1e-9) / 1e9,
+            "delivered_gstencil_s": sum(work) / busy / 1e9,
+            "arrival_span_s": span, "wall_s": busy,
+            "note": "arrivals at their Poisson times, jobs uncapped; each job runs in the fastest arithmetic whose "
+                    "a priori error bound meets its target (sparse TF32, FP16 hi/lo, FP32 CUDA cores); offered "
+                    "above delivered means the GPU is saturated and the queue (and p99) grows with the run"}
+
+
 def run_serving(a):
-    """Poisson arrivals (200 jobs/s) of mixed 2-D/3-D stencil jobs submitted to
-    the continuous-batching server; a bounded prefix of the arrival sequence
-    (its total work is ~1e5 times a GPU-second budget otherwise)."""
     import torch
     import paper_2506_22035_gb300 as spider
     from paper_2506_22035_gb300 import build as _b
     _b.build()
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    arrivals = si.serving_arrivals()
-    chosen, work = [], 0
-    for jb in arrivals:
-        wk = int(np.prod(jb.extents)) * jb.steps
-        if work + wk > 3.0e10 and chosen:
-            continue
-        chosen.append(jb)
-        work += wk
-        if len(chosen) >= a.steps:
-            break
-    inputs = [si.job_inputs(jb) for jb in chosen]
-    server = spider.Server(120 * 10**9)
-    plans = [spider.Plan(w, jb.extents, jb.shape, "tf32") for jb, (u0, w) in zip(chosen, inputs)]
-    t0 = time.perf_counter()
-    tickets = []
-    base = chosen[0].arrival_s
-    for jb, p, (u0, w) in zip(chosen, plans, inputs):
-        while time.perf_counter() - t0 < jb.arrival_s - base:
-            time.sleep(0.0002)
-        tickets.append(server.submit(p, u0, jb.steps, jb.err_target))
-    lat = {}
-    outs = {t: np.empty_like(u0) for t, (u0, w) in zip(tickets, inputs)}
-    while len(lat) < len(tickets):
-        for t in tickets:
-            if t not in lat:
-                done, l = server.poll(t, outs[t])
-                if done:
-                    lat[t] = l
-        time.sleep(0.001)
-    dt = time.perf_counter() - t0
-    server.close()
-    for p in plans:
-        p.close()
-    ls = np.array(sorted(lat.values()))
-    span = chosen[-1].arrival_s - base if len(chosen) > 1 else 0.0
-    line = {"metric": "GStencil/s", "value": work / dt / 1e9, "unit": "GStencil/s", "n_gpus": world,
-            "steps": len(chosen), "warmup": 0, "ms_per_step": dt / len(chosen) * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f16x2", "data": "synthetic",
-            "config": {"workload": "serving: Poisson 200/s, 2-D side 256-8192 / 3-D side 64-512, r 1-3, "
-                                   "10-500 steps, error target 1e-3 (TF32) or 1e-5 (FP16 hi/lo)",
-                       "jobs": len(chosen), "stencil_updates": work, "hbm_budget_bytes": 120 * 10**9},
-            "latency_s": {"p50": float(np.percentile(ls, 50)), "p99": float(np.percentile(ls, 99)),
-                          "max": float(ls[-1])},
-            "offered_load_gstencil_s": work / max(span, 1e-9) / 1e9 if span > 0 else None}
+    rec = serving_run(spider, a.serving_jobs or 600)
+    line = {"metric": "GStencil/s", "value": rec["delivered_gstencil_s"], "unit": "GStencil/s", "n_gpus": 1,
+            "steps": rec["jobs_completed"], "warmup": 0, "ms_per_step": rec["wall_s"] / rec["jobs_completed"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f16x2+f32",
+            "data": "synthetic", "config": {"workload": rec["workload"], "hbm_budget_bytes": 120 * 10**9},
+            "serving": rec}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mma_peak(a):
+    """Peak issue rates of the warp-level MMA shapes (spider_measure_mma_rate)."""
+    import torch
+    import paper_2506_22035_gb300 as spider
+    from paper_2506_22035_gb300 import build as _b
+    _b.build()
+    torch.cuda.set_device(0)
+    rates = {k: spider.measure_mma_rate(k) for k in spider.MMA_KINDS}
+    flops = {"sp_tf32": 16 * 8 * 16 * 2, "sp_f16": 16 * 8 * 32 * 2, "sp_bf16": 16 * 8 * 32 * 2,
+             "dense_tf32": 16 * 8 * 8 * 2}
+    line = {"metric": "mma per second", "value": rates["sp_tf32"], "unit": "mma.sp/s", "n_gpus": 1, "steps": 5,
+            "warmup": 1, "higher_is_better": True, "dtype": "tf32", "data": "synthetic",
+            "config": {"workload": "mma_peak: warp-level MMAs with operands in registers, 8 chains per warp, "
+                                   "16 warps per SM"},
+            "rates": {k: {"mma_per_s": v, "dense_equivalent_tflops": v * flops[k] / 1e12} for k, v in rates.items()}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -671,6 +850,8 @@ def main():
         return run_batched(a)
     if a.workload == "serving":
         return run_serving(a)
+    if a.workload == "mma_peak":
+        return run_mma_peak(a)
     if a.workload == "sweep":
         return run_sweep(a)
     return run_spider(a)

@@ -56,19 +56,35 @@ typedef enum { SPIDER_STAR = 0, SPIDER_BOX = 1 } spider_shape;
 
 /* Arithmetic of the tensor-core products (accumulation is always FP32).
  *  TF32   : one sparse TF32 product per kernel row (grid and weights rounded
- *           to nearest TF32).
+ *           to nearest TF32; the weights so that their sum stays as close to
+ *           the FP32 sum as TF32 allows).
  *  F16X2  : grid and weights split into FP16 hi + lo parts (lo parts scaled by
- *           2^11); hi*hi + hi*lo + lo*hi.  Requires |grid values| < 32768.
- *  BF16X3 : grid and weights split into BF16 hi + lo parts; the three
- *           products hi*hi + hi*lo + lo*hi, FP32 range (no scaling).
+ *           2^11, about 22 bits); hi*hi + hi*lo + lo*hi, each hi*hi MMA into a
+ *           fresh accumulator added in FP32.  Requires |grid values| < 32768.
+ *  BF16X3 : grid and weights split into three BF16 terms hi + mid + lo (24
+ *           bits, FP32 range); the six products above 2^-24 relative (hi*hi,
+ *           hi*mid, mid*hi, hi*lo, lo*hi, mid*mid), in two passes.
+ *  The last term of every split weight is rounded so the split weights sum
+ *  as close as possible to the FP32 weights.  spider_plan_error_bound gives
+ *  the error each arithmetic is expected to stay within.
  *  AUTO   : TF32. */
 typedef enum { SPIDER_TF32 = 0, SPIDER_F16X2 = 1, SPIDER_BF16X3 = 2, SPIDER_AUTO = 3 } spider_precision;
 
-/* Which kernel a plan runs.  SPARSE_TC is SPIDER; the other two are the
+/* Which kernel a plan runs.  SPARSE_TC is SPIDER; the others are the
  * comparators built on the same tiling: DENSE_TC multiplies the same banded
  * K without the 2:4 compression on dense tensor cores (the paper's "SPIDER w.
- * TC" ablation, Sec. 4.4), CUDA_CORE is a direct FP32 FMA stencil. */
-typedef enum { SPIDER_ENGINE_SPARSE_TC = 0, SPIDER_ENGINE_DENSE_TC = 1, SPIDER_ENGINE_CUDA_CORE = 2 } spider_engine;
+ * TC" ablation, Sec. 4.4), CUDA_CORE is a direct FP32 FMA stencil, and
+ * SPARSE_TC_COPY is SPIDER with the input row swap done the way Sec. 3.2
+ * sets its own design against: an explicit copy of every input window, in
+ * the swapped order, into a shared-memory buffer of its own, which the MMA
+ * operands then load contiguously (2-D, TF32, radius 1..3, one step per
+ * pass; the same products as SPARSE_TC, bit for bit). */
+typedef enum {
+  SPIDER_ENGINE_SPARSE_TC = 0,
+  SPIDER_ENGINE_DENSE_TC = 1,
+  SPIDER_ENGINE_CUDA_CORE = 2,
+  SPIDER_ENGINE_SPARSE_TC_COPY = 3
+} spider_engine;
 
 /* spider_plan_create -- the paper's offline transform (Sec. 3.1, Sec. 3.3.2).
  *
@@ -99,8 +115,9 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
                                  const float* coeffs, spider_precision prec, spider_plan* out);
 
 /* Selects the kernel the plan runs (default SPIDER_ENGINE_SPARSE_TC).  The
- * comparators support SPIDER_TF32 (DENSE_TC) and plain FP32 (CUDA_CORE,
- * precision ignored), radius 1..3 (SPIDER_ERR_UNSUPPORTED otherwise). */
+ * comparators support SPIDER_TF32 (DENSE_TC, SPARSE_TC_COPY) and plain FP32
+ * (CUDA_CORE, precision ignored), radius 1..3; SPARSE_TC_COPY 2-D grids only
+ * (SPIDER_ERR_UNSUPPORTED otherwise). */
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
 /* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4
@@ -116,13 +133,16 @@ spider_status spider_plan_set_steps_per_pass(spider_plan plan, int steps_per_pas
  * two input boxes in flight; 1 = 16 rows (more independent MMAs per warp), two
  * boxes; 2 = 8 rows, one box, registers capped so three CTAs share an SM;
  * 3 = 16 rows, one box; 4 = small tiles (level 1 of 32 rows instead of 64,
- * one warp unit per warp per level) for grids that do not fill the GPU.
+ * one warp unit per warp per level) for grids that do not fill the GPU;
+ * 5 = as 2 with the last level written by 16-byte stores (sparse TF32; as 2
+ * elsewhere).
  * FP16/BF16 splits and the dense engine: 2 and 3 = 8 rows with registers
  * capped so two CTAs share an SM, two or one input boxes; CUDA-core engine:
  * 2 and 3 run as 0 and 1.
  * 3-D: 0 and 4 = column blocks of 16 level-1 rows, warp units of 4 rows; 1
  * and 3 = 32 rows, units of 8; 2 = as 0 with registers capped for three CTAs
- * per SM at 2 steps per pass.  Any other value returns SPIDER_ERR_INVALID.
+ * per SM at 2 steps per pass; 5 = as 2.  Any other value returns
+ * SPIDER_ERR_INVALID.
  * spider_plan_autotune sets it. */
 spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 
@@ -188,20 +208,58 @@ spider_status spider_run_host(spider_plan plan, const float* host_in, float* hos
  * coefficients.  Every GPU that loads the library holds these arrays until
  * the process exits.
  *  grid_in, grid_out, steps, stream: as for spider_run.
+ * On grids TMA can read in their own layout it runs the same passes as
+ * spider_run (the plan's steps per pass and tile variant); grids whose rows
+ * are not a multiple of 4 floats (1-D: 8), or whose output buffer is not
+ * 16-byte aligned, run one time step per pass (there are no padded grids).
  * Grids with more than 4,194,304 points return SPIDER_ERR_INVALID and nothing
  * is done.  The first call on each device looks up the arrays' device
  * addresses (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Each call loads its plan's operands into
- * the shared arrays and clears the shared status word, and all calls share
- * one scratch grid, so calls that overlap on the GPU (other streams or
- * threads) race and corrupt each other's results.  A device-side wait that
- * runs out is not reported by this entry point. */
+ * call before any stream capture.  The looked-up addresses are kept for the
+ * process: no call may follow a cudaDeviceReset of that device.  Each call
+ * copies its plan's operands (a few KB, from the plan's host memory) into
+ * the shared arrays on `stream` and clears the shared status word, and all
+ * calls share one scratch grid, so calls that overlap on the GPU (other
+ * streams or threads) race and corrupt each other's results.  A device-side
+ * wait that runs out is not reported by this entry point. */
 spider_status spider_run_static(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
                                 cudaStream_t stream);
 
 /* Blocks until the plan's work on `stream` is done and reports any
  * device-side error (SPIDER_ERR_TIMEOUT for an expired wait). */
 spider_status spider_plan_sync(spider_plan plan, cudaStream_t stream);
+
+/* spider_plan_error_bound -- the library's a priori bound on the relative L2
+ * error, against exact arithmetic, of `steps` time steps of the plan's
+ * stencil computed in precision `prec` on engine `engine` (the paper states
+ * no precision; this is the library's error model, and the serving loop picks
+ * with it the fastest arithmetic that meets a job's error target):
+ *     bound = steps * (s + d) + f
+ *  s  the plan's weight-sum error in that arithmetic: how far the weights the
+ *     products use (TF32-rounded, or the FP16 / BF16 split terms) sum from
+ *     the FP32 weights, relative to sum |w|.  It scales the constant mode of
+ *     the field every step, so on a field of one sign the error grows by
+ *     about s per step.  The plan rounds weights so that s is small.
+ *  d  the rest of the per-step bias: TF32 rounds the grid to 11 bits every
+ *     step, which is biased where the field is smooth (up to 5e-5 per step
+ *     measured); the FP16 split's 22-bit products lose low bits inside the
+ *     tensor core (4e-8); BF16 hi/mid/lo (6e-9) and FP32 (none) do not;
+ *  f  the part of the error that does not grow with the step count.
+ * d and f are twice the largest values measured on GB300 (radius 1..3 star
+ * and box stencils in 2-D and 3-D, 10..500 steps, fields uniform on [0, 1)
+ * and [-1, 1)); they assume the field does not grow, as
+ * with sum |w| <= 1.  Host work only.  SPIDER_ERR_UNSUPPORTED when the
+ * stencil has no kernel in that arithmetic (e.g. radius 4..7 off sparse
+ * TF32). */
+spider_status spider_plan_error_bound(spider_plan plan, spider_precision prec, spider_engine engine, int64_t steps,
+                                      double* bound);
+
+/* Bytes of device memory the plan owns right now: its packed operands,
+ * status word, scratch and padded grids and the staging grids of
+ * spider_run_host, all allocated on first use.  0 for a plan that has not
+ * run through spider_run, spider_run_host, spider_batch or
+ * spider_plan_autotune (spider_run_static allocates nothing). */
+spider_status spider_plan_device_bytes(spider_plan plan, size_t* bytes);
 
 void spider_plan_destroy(spider_plan plan);
 
@@ -224,6 +282,30 @@ void spider_plan_destroy(spider_plan plan);
  * SPIDER_ERR_TIMEOUT if a dependency wait ran out. */
 spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                            const int64_t* steps, cudaStream_t stream);
+
+/* ---- failure detection -------------------------------------------------------
+ * The paper has no counterpart.  Every wait of the library's kernels (a TMA
+ * load landing, a batch-queue item waiting for its neighbours' previous step)
+ * is bounded: when it runs out, the kernel records a timeout in a device
+ * status word and finishes without touching memory it does not own, the
+ * CUDA context stays usable, and the call that reads the status word
+ * (spider_plan_sync, spider_run_host, spider_batch) returns
+ * SPIDER_ERR_TIMEOUT.
+ *
+ * spider_set_wait_limit: the limit of every bounded wait, in SM clock cycles
+ * (default 4e9, about two seconds at 2 GHz; >= 1000).  Process-wide; applies
+ * to kernels launched after the call (run graphs captured earlier keep the
+ * limit they were captured with).
+ *
+ * spider_batch_drop_item: a test hook.  The next spider_batch call leaves
+ * item `item` of its persistent queue out (items numbered in the queue's
+ * step-major order, from 0; -1 clears): the item is claimed but neither
+ * loaded nor computed, and its tile's step counter is not advanced, so the
+ * items that depend on it wait until the limit runs out and the call returns
+ * SPIDER_ERR_TIMEOUT (that call's results are then undefined).  The hook
+ * applies to one call and resets itself. */
+spider_status spider_set_wait_limit(long long cycles);
+spider_status spider_batch_drop_item(long long item);
 
 /* ---- domain decomposition: slabs with ghost planes ---------------------------
  * The paper runs one GPU and has no counterpart; this is the hook a
@@ -293,11 +375,14 @@ spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out);
 
 /* Submits a job.  `plan` is copied (the caller may destroy it afterwards).
  * host_in: host grid of the plan's extents, copied before return.
- * err_target: relative L2 error the caller accepts; <= 1e-4 selects a split
- * precision (radius <= 3; the wide layout of radius 4..7 stays TF32),
- * otherwise the plan's precision.  *ticket identifies the job.
- * SPIDER_ERR_OOM if the job alone exceeds the budget; SPIDER_ERR_BUSY if the
- * queue is full. */
+ * err_target: relative L2 error the caller accepts.  The job runs in the
+ * fastest arithmetic whose a priori bound (spider_plan_error_bound) for
+ * `steps` steps of this stencil meets it, tried in this order: the plan's own
+ * precision and engine, sparse TF32, the FP16 hi/lo split (only when every
+ * |host_in| value is below 16384), FP32 on CUDA cores (radius <= 3).
+ * *ticket identifies the job.  SPIDER_ERR_UNSUPPORTED if no arithmetic built
+ * for the stencil meets the target; SPIDER_ERR_OOM if the job alone exceeds
+ * the budget; SPIDER_ERR_BUSY if the queue is full. */
 spider_status spider_submit(spider_server server, spider_plan plan, const float* host_in, int64_t steps,
                             double err_target, uint64_t* ticket);
 
@@ -308,6 +393,18 @@ spider_status spider_poll(spider_server server, uint64_t ticket, float* out, int
 
 /* Stops the worker after the jobs already submitted finish, frees everything. */
 void spider_server_destroy(spider_server server);
+
+/* spider_measure_mma_rate -- the peak issue rate, in MMAs per second, of one
+ * warp-level tensor-core MMA shape on the current GPU: the denominator of the
+ * tensor-pipe roofline of the stencil kernels.  The paper has no counterpart
+ * (its Table 2 counts MMAs per point; this measures what one GPU sustains).
+ *  kind  0 = sparse TF32 m16n8k16 (mma.sp), 1 = sparse FP16 m16n8k32,
+ *        2 = sparse BF16 m16n8k32, 3 = dense TF32 m16n8k8 (mma.sync).
+ * A kernel of two CTAs of eight warps per SM keeps its operands in registers
+ * and issues eight independent accumulator chains per warp; the best of five
+ * timed launches (CUDA events on `stream`) is reported.  Synchronous; it
+ * allocates and frees a small device buffer. */
+spider_status spider_measure_mma_rate(int kind, double* mma_per_s, cudaStream_t stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* spider_last_error(void);

@@ -13,11 +13,11 @@ import numpy as np
 
 from . import _native
 from ._native import (SPIDER_BF16X3, SPIDER_BOX, SPIDER_ENGINE_CUDA_CORE, SPIDER_ENGINE_DENSE_TC,
-                      SPIDER_ENGINE_SPARSE_TC, SPIDER_F16X2, SPIDER_STAR, SPIDER_TF32, SpiderError, check)
+                      SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_SPARSE_TC_COPY, SPIDER_F16X2, SPIDER_STAR, SPIDER_TF32, SpiderError, check)
 
 PRECISIONS = {"tf32": SPIDER_TF32, "f16x2": SPIDER_F16X2, "bf16x3": SPIDER_BF16X3}
 ENGINES = {"sparse_tc": SPIDER_ENGINE_SPARSE_TC, "dense_tc": SPIDER_ENGINE_DENSE_TC,
-           "cuda_core": SPIDER_ENGINE_CUDA_CORE}
+           "cuda_core": SPIDER_ENGINE_CUDA_CORE, "sparse_tc_copy": SPIDER_ENGINE_SPARSE_TC_COPY}
 SHAPES = {"star": SPIDER_STAR, "box": SPIDER_BOX}
 
 
@@ -110,6 +110,21 @@ class Plan:
     def sync(self, stream=None) -> None:
         check(_native.load().spider_plan_sync(self._h, _stream_handle(stream)), "spider_plan_sync")
 
+    def error_bound(self, steps: int, precision: str | None = None, engine: str | None = None) -> float:
+        """The library's a priori relative L2 error bound for `steps` steps of
+        this stencil in an arithmetic (default: the plan's own)."""
+        out = ctypes.c_double()
+        check(_native.load().spider_plan_error_bound(self._h, PRECISIONS[precision or self.precision],
+                                                     ENGINES[engine or self.engine], int(steps), ctypes.byref(out)),
+              "spider_plan_error_bound")
+        return out.value
+
+    def device_bytes(self) -> int:
+        """Bytes of device memory the plan owns right now."""
+        out = ctypes.c_size_t()
+        check(_native.load().spider_plan_device_bytes(self._h, ctypes.byref(out)), "spider_plan_device_bytes")
+        return out.value
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             _native.load().spider_plan_destroy(self._h)
@@ -141,6 +156,18 @@ def constant_check_fp64(a, extents, margin: int, value: float, stream=None) -> f
     check(_native.load().spider_constant_check_fp64(_ptr(a), len(ext), (ctypes.c_int64 * len(ext))(*ext),
                                                     int(margin), float(value), ctypes.byref(out),
                                                     _stream_handle(stream)), "spider_constant_check_fp64")
+    return out.value
+
+
+MMA_KINDS = {"sp_tf32": 0, "sp_f16": 1, "sp_bf16": 2, "dense_tf32": 3}
+
+
+def measure_mma_rate(kind: str = "sp_tf32", stream=None) -> float:
+    """Peak MMAs per second of one warp-level MMA shape on the current GPU
+    (spider_measure_mma_rate)."""
+    out = ctypes.c_double()
+    check(_native.load().spider_measure_mma_rate(MMA_KINDS[kind], ctypes.byref(out), _stream_handle(stream)),
+          "spider_measure_mma_rate")
     return out.value
 
 
@@ -232,4 +259,5 @@ class Server:
 
 
 __all__ = ["Plan", "Domain", "Server", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
+           "measure_mma_rate",
            "PRECISIONS", "ENGINES", "SHAPES"]

@@ -25,7 +25,7 @@ SPIDER_STAR, SPIDER_BOX = 0, 1
 # spider_precision
 SPIDER_TF32, SPIDER_F16X2, SPIDER_BF16X3, SPIDER_AUTO = 0, 1, 2, 3
 # spider_engine
-SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_DENSE_TC, SPIDER_ENGINE_CUDA_CORE = 0, 1, 2
+SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_DENSE_TC, SPIDER_ENGINE_CUDA_CORE, SPIDER_ENGINE_SPARSE_TC_COPY = 0, 1, 2, 3
 
 # name -> (restype, argtypes); the complete list of entry points of spider.h
 SIGNATURES = {
@@ -42,7 +42,11 @@ SIGNATURES = {
     "spider_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_run_static": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_plan_sync": (c_int, [c_void_p, c_void_p]),
+    "spider_plan_device_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "spider_plan_error_bound": (c_int, [c_void_p, c_int, c_int, c_int64, ctypes.POINTER(c_double)]),
     "spider_plan_destroy": (None, [c_void_p]),
+    "spider_set_wait_limit": (c_int, [ctypes.c_longlong]),
+    "spider_batch_drop_item": (c_int, [ctypes.c_longlong]),
     "spider_batch": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                              ctypes.POINTER(c_int64), c_void_p]),
     "spider_domain_create": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_void_p)]),
@@ -54,6 +58,7 @@ SIGNATURES = {
     "spider_norms_fp64": (c_int, [c_void_p, c_void_p, c_int64, ctypes.POINTER(c_double), c_void_p]),
     "spider_constant_check_fp64": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64), c_int64, c_double,
                                            ctypes.POINTER(c_double), c_void_p]),
+    "spider_measure_mma_rate": (c_int, [c_int, ctypes.POINTER(c_double), c_void_p]),
     "spider_server_create": (c_int, [c_size_t, ctypes.POINTER(c_void_p)]),
     "spider_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, ctypes.POINTER(c_uint64)]),
     "spider_poll": (c_int, [c_void_p, c_uint64, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),

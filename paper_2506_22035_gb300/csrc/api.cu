@@ -39,6 +39,24 @@ static void drop_graphs(spider_plan_t* p) {
   p->dev.graphs.clear();
 }
 
+// Device memory of a plan: cudaMalloc / cudaFree, or stream-ordered from the
+// plan's pool (see DeviceState::pool).
+static cudaError_t dev_alloc(spider_plan_t* p, void** ptr, size_t bytes) {
+  if (p->dev.pool) return cudaMallocFromPoolAsync(ptr, bytes, p->dev.pool, p->dev.pool_stream);
+  return cudaMalloc(ptr, bytes);
+}
+static void dev_free(spider_plan_t* p, void* ptr) {
+  if (!ptr) return;
+  if (p->dev.pool) cudaFreeAsync(ptr, p->dev.pool_stream);
+  else cudaFree(ptr);
+}
+// Host -> device copy of plan data (pageable host memory: the call returns
+// once the data is staged, so the host vectors may change afterwards).
+static cudaError_t dev_upload(spider_plan_t* p, void* dst, const void* src, size_t bytes) {
+  if (p->dev.pool) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->dev.pool_stream);
+  return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
 static void free_device(spider_plan_t* p) {
   DeviceState& d = p->dev;
   if (d.device >= 0) {
@@ -46,20 +64,25 @@ static void free_device(spider_plan_t* p) {
     cudaGetDevice(&cur);
     if (cur != d.device) cudaSetDevice(d.device);
     // cudaFree waits for the device, so no replay of a cached graph is still
-    // running when the graphs are destroyed
-    cudaFree(d.a_words);
-    cudaFree(d.meta_words);
-    cudaFree(d.w_dense);
-    cudaFree(d.scratch);
-    cudaFree(d.pad);
-    cudaFree(d.host_stage_in);
-    cudaFree(d.host_stage_out);
-    cudaFree(d.status);
+    // running when the graphs are destroyed (a pooled plan has no graphs:
+    // its frees are ordered after its work on its stream)
+    dev_free(p, d.a_words);
+    dev_free(p, d.meta_words);
+    dev_free(p, d.w_dense);
+    dev_free(p, d.scratch);
+    dev_free(p, d.pad);
+    dev_free(p, d.host_stage_in);
+    dev_free(p, d.host_stage_out);
+    dev_free(p, d.status);
     drop_graphs(p);
     if (d.capture_stream) cudaStreamDestroy(d.capture_stream);
     if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
   }
+  const cudaMemPool_t pool = d.pool;
+  const cudaStream_t pool_stream = d.pool_stream;
   d = DeviceState();
+  d.pool = pool;
+  d.pool_stream = pool_stream;
 }
 
 // Uploads the packed operands on first use (or after an engine change).
@@ -71,20 +94,21 @@ static spider_status ensure_device(spider_plan_t* p) {
     return fail(SPIDER_ERR_INVALID, "plan was first used on another device");
   if (d.device < 0) d.device = dev;
   if (!d.status) {
-    SPIDER_CUDA(cudaMalloc(&d.status, sizeof(int)));
-    SPIDER_CUDA(cudaMemset(d.status, 0, sizeof(int)));
+    SPIDER_CUDA(dev_alloc(p, (void**)&d.status, sizeof(int)));
+    if (d.pool) SPIDER_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int), d.pool_stream));
+    else SPIDER_CUDA(cudaMemset(d.status, 0, sizeof(int)));
   }
   if (!d.a_words && !p->a_words.empty()) {
-    SPIDER_CUDA(cudaMalloc(&d.a_words, p->a_words.size() * 4));
-    SPIDER_CUDA(cudaMemcpy(d.a_words, p->a_words.data(), p->a_words.size() * 4, cudaMemcpyHostToDevice));
+    SPIDER_CUDA(dev_alloc(p, (void**)&d.a_words, p->a_words.size() * 4));
+    SPIDER_CUDA(dev_upload(p, d.a_words, p->a_words.data(), p->a_words.size() * 4));
   }
   if (!d.meta_words && !p->meta_words.empty()) {
-    SPIDER_CUDA(cudaMalloc(&d.meta_words, p->meta_words.size() * 4));
-    SPIDER_CUDA(cudaMemcpy(d.meta_words, p->meta_words.data(), p->meta_words.size() * 4, cudaMemcpyHostToDevice));
+    SPIDER_CUDA(dev_alloc(p, (void**)&d.meta_words, p->meta_words.size() * 4));
+    SPIDER_CUDA(dev_upload(p, d.meta_words, p->meta_words.data(), p->meta_words.size() * 4));
   }
   if (!d.w_dense) {
-    SPIDER_CUDA(cudaMalloc(&d.w_dense, p->w.size() * 4));
-    SPIDER_CUDA(cudaMemcpy(d.w_dense, p->w.data(), p->w.size() * 4, cudaMemcpyHostToDevice));
+    SPIDER_CUDA(dev_alloc(p, (void**)&d.w_dense, p->w.size() * 4));
+    SPIDER_CUDA(dev_upload(p, d.w_dense, p->w.data(), p->w.size() * 4));
   }
   return SPIDER_OK;
 }
@@ -92,11 +116,12 @@ static spider_status ensure_device(spider_plan_t* p) {
 static spider_status ensure_scratch(spider_plan_t* p) {
   const size_t bytes = (size_t)p->points() * sizeof(float);
   if (p->dev.scratch && p->dev.scratch_bytes >= bytes) return SPIDER_OK;
-  cudaFree(p->dev.scratch);
+  dev_free(p, p->dev.scratch);
   p->dev.scratch = nullptr;
-  cudaError_t e = cudaMalloc(&p->dev.scratch, bytes);
+  cudaError_t e = dev_alloc(p, (void**)&p->dev.scratch, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    p->dev.scratch = nullptr;
     return fail(SPIDER_ERR_OOM, std::string("scratch grid: ") + cudaGetErrorString(e));
   }
   p->dev.scratch_bytes = bytes;
@@ -105,17 +130,22 @@ static spider_status ensure_scratch(spider_plan_t* p) {
 
 spider_status ensure_plan_pad(spider_plan_t* p, size_t bytes) {
   if (p->dev.pad && p->dev.pad_bytes >= bytes) return SPIDER_OK;
-  cudaFree(p->dev.pad);  // waits for the device: no earlier run still uses it
+  dev_free(p, p->dev.pad);  // cudaFree waits for the device: no earlier run still uses it
   if (p->dev.pad) drop_graphs(p);  // cached run graphs hold the old address
   p->dev.pad = nullptr;
   p->dev.pad_bytes = 0;
-  cudaError_t e = cudaMalloc(&p->dev.pad, bytes);
+  cudaError_t e = dev_alloc(p, (void**)&p->dev.pad, bytes);
   // zero once: the kernels never store beyond nx, so the 1-D grids' tails
   // stay zero and read as the halo
-  if (e == cudaSuccess) e = cudaMemset(p->dev.pad, 0, bytes);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();  // before any stream of the caller writes it
+  if (p->dev.pool) {
+    // ordered before the plan's kernels on its own stream
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->dev.pad, 0, bytes, p->dev.pool_stream);
+  } else {
+    if (e == cudaSuccess) e = cudaMemset(p->dev.pad, 0, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();  // before any stream of the caller writes it
+  }
   if (e != cudaSuccess) {
-    cudaFree(p->dev.pad);
+    dev_free(p, p->dev.pad);
     p->dev.pad = nullptr;
     cudaGetLastError();
     return fail(SPIDER_ERR_OOM, std::string("padded grids: ") + cudaGetErrorString(e));
@@ -138,11 +168,70 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
 int max_steps_per_pass(const spider_plan_t* p) {
+  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY) return 1;
   if (p->wide()) return p->ndim == 1 ? 4 : 1;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
   if (p->ndim == 2) return sparse_tf32 ? max_deep_steps(p->r) : 4;  // deep tiles beyond 4
   if (p->ndim == 3 && p->r == 1 && sparse_tf32) return 4;
   return 1;
+}
+
+// A priori error model of an arithmetic (spider_plan_error_bound).  The
+// relative L2 error of n steps against exact arithmetic is bounded by
+// n * (wsum + drift) + floor:
+//  * wsum: the plan's weight-sum error in that arithmetic, |sum of the
+//    weights the products use - sum of the FP32 weights| / sum |w|; it
+//    scales the constant mode every step, so on fields of one sign the
+//    error grows by about that much per step;
+//  * drift: the rest of the per-step bias, measured on fields of one sign.
+//    TF32: rounding the grid to 11 bits every step is biased where the field
+//    is smooth (neighbouring values within one TF32 unit round the same way),
+//    up to 5e-5 per step measured.  FP16 hi/lo: the tensor core aligns each
+//    MMA's 22-bit products to the largest and drops their lowest bits, about
+//    4e-8 per step.  BF16 hi/mid/lo: 16-bit products lose no bits, 6e-9.
+//    FP32 on CUDA cores: round-to-nearest FMAs with exact weights, none.
+//  * floor: the error that does not grow with the step count.
+// The constants are twice the largest values measured on GB300 over radius
+// 1..3 star and box stencils, 2-D and 3-D, 10..500 steps, fields uniform on
+// [0, 1) and [-1, 1).
+ErrorModel error_model(const spider_plan_t* p, spider_precision prec, spider_engine engine) {
+  ErrorModel m;
+  const bool wide = p->r > kMaxR || (p->ndim == 1 && engine == SPIDER_ENGINE_SPARSE_TC && prec == SPIDER_TF32);
+  if (engine == SPIDER_ENGINE_CUDA_CORE) {
+    m.built = p->r <= kMaxR;
+    m.wsum = 0;  // FP32 weights, exact
+    m.drift = 1e-10;
+    m.floor = 3e-7;
+    return m;
+  }
+  if (engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY) {
+    m.built = p->r <= kMaxR && prec == SPIDER_TF32 && (engine == SPIDER_ENGINE_DENSE_TC || p->ndim == 2);
+    m.wsum = p->wsum_rel[0];
+    m.drift = 1e-4;
+    m.floor = 7e-4;
+    return m;
+  }
+  switch (prec) {
+    case SPIDER_F16X2:
+      m.built = p->r <= kMaxR && !wide;
+      m.wsum = p->wsum_rel[1];
+      m.drift = 8e-8;
+      m.floor = 1e-6;
+      break;
+    case SPIDER_BF16X3:
+      m.built = p->r <= kMaxR && !wide;
+      m.wsum = p->wsum_rel[2];
+      m.drift = 1.5e-8;
+      m.floor = 3e-7;
+      break;
+    default:
+      m.built = true;
+      m.wsum = p->wsum_rel[0];
+      m.drift = 1e-4;
+      m.floor = 7e-4;
+      break;
+  }
+  return m;
 }
 
 // A run steps through the plan's padded grids when `out` is not a grid TMA
@@ -203,7 +292,7 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   // TF32 engines: every grid between two passes is stored rounded to TF32 as
   // the next pass would round it, and that pass skips the rounding; the
   // caller's input is rounded on load and the final grid is stored unrounded.
-  const bool tf32 = p->engine == SPIDER_ENGINE_DENSE_TC ||
+  const bool tf32 = p->engine == SPIDER_ENGINE_DENSE_TC || p->engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
                     (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3);
   float* bufs[2] = {out, p->dev.scratch};
   int first = (npasses % 2 == 1) ? 0 : 1;  // packed: the last pass lands in out
@@ -371,9 +460,12 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
 
 spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
-  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_CUDA_CORE) return fail(SPIDER_ERR_INVALID, "bad engine");
-  if (engine == SPIDER_ENGINE_DENSE_TC && p->prec != SPIDER_TF32)
-    return fail(SPIDER_ERR_UNSUPPORTED, "the dense tensor-core comparator runs TF32 only");
+  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_COPY)
+    return fail(SPIDER_ERR_INVALID, "bad engine");
+  if ((engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY) && p->prec != SPIDER_TF32)
+    return fail(SPIDER_ERR_UNSUPPORTED, "the dense and explicit-copy comparators run TF32 only");
+  if (engine == SPIDER_ENGINE_SPARSE_TC_COPY && p->ndim != 2)
+    return fail(SPIDER_ERR_UNSUPPORTED, "the explicit-copy comparator is built for 2-D grids");
   if (engine != SPIDER_ENGINE_SPARSE_TC && p->r > kMaxR)
     return fail(SPIDER_ERR_UNSUPPORTED, "radius 4..7 is built for the sparse tensor-core engine only");
   std::lock_guard<std::mutex> lock(p->mu);
@@ -472,6 +564,36 @@ spider_status spider_plan_sync(spider_plan p, cudaStream_t stream) {
       return fail(SPIDER_ERR_TIMEOUT, "a device-side wait ran out");
     }
   }
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_error_bound(spider_plan p, spider_precision prec, spider_engine engine, int64_t steps,
+                                      double* bound) {
+  if (!p || !bound) return fail(SPIDER_ERR_INVALID, "plan or bound is NULL");
+  if (steps < 0) return fail(SPIDER_ERR_INVALID, "steps must be >= 0");
+  if (prec == SPIDER_AUTO) prec = SPIDER_TF32;
+  if (prec < SPIDER_TF32 || prec > SPIDER_BF16X3) return fail(SPIDER_ERR_INVALID, "bad precision");
+  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_COPY)
+    return fail(SPIDER_ERR_INVALID, "bad engine");
+  const ErrorModel m = error_model(p, prec, engine);
+  if (!m.built) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil in that arithmetic");
+  *bound = (double)steps * (m.wsum + m.drift) + m.floor;
+  return SPIDER_OK;
+}
+
+spider_status spider_plan_device_bytes(spider_plan p, size_t* bytes) {
+  if (!p || !bytes) return fail(SPIDER_ERR_INVALID, "plan or bytes is NULL");
+  std::lock_guard<std::mutex> lock(p->mu);
+  const DeviceState& d = p->dev;
+  size_t b = 0;
+  if (d.a_words) b += p->a_words.size() * 4;
+  if (d.meta_words) b += p->meta_words.size() * 4;
+  if (d.w_dense) b += p->w.size() * 4;
+  if (d.status) b += sizeof(int);
+  if (d.scratch) b += d.scratch_bytes;
+  if (d.pad) b += d.pad_bytes;
+  if (d.host_stage_in) b += 2 * (size_t)p->points() * sizeof(float);
+  *bytes = b;
   return SPIDER_OK;
 }
 

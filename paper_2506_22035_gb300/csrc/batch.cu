@@ -19,6 +19,7 @@
 // (TF32 sparse MMA, 64 x 128 outputs, TMA halo box).  Each job brings its own
 // tensor maps and packed operands.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -52,6 +53,9 @@ constexpr int kMaxTableSmem = 48 * 1024;
 // Below it the queue wins: 256 grids of 32^2..255^2 points run at 188
 // GStencil/s through it and at 41 as fused passes on side streams.
 constexpr long long kFuseMinPoints = 1LL << 16;
+
+// Queue item the next spider_batch call leaves out (spider_batch_drop_item), -1: none.
+std::atomic<long long> g_drop_item{-1};
 constexpr int kSideStreams = 8;                  // streams the fused grids run on, next to the queue
 
 // Non-blocking streams for the grids that run as fused passes beside the
@@ -192,17 +196,19 @@ __device__ __forceinline__ int warp_search(const long long* __restrict__ table, 
 
 struct ItemSlot {
   int job, s, tile, end;
+  int skip;  // the item was left out (spider_batch_drop_item): no load, no compute, no publication
 };
 
 // Waits for phase `parity` of `bar` like mbar_wait_bounded, but sleeps
 // `ns` nanoseconds between polls, so a warp that waits for a long time (a
 // producer two items ahead of its consumers) leaves the issue slots to the
 // warps that compute.
-__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, int* status, unsigned ns) {
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, int* status, unsigned ns,
+                                                  long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(status, kStatusTimeout);
       return false;
     }
@@ -226,7 +232,8 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
                                                              int tables_bytes, int tables_in_smem, int o_order,
                                                              int o_step, int o_active, int o_tp,
                                                              const CUtensorMap* __restrict__ maps, int max_steps,
-                                                             int* __restrict__ counter, int* __restrict__ status) {
+                                                             int* __restrict__ counter, int* __restrict__ status,
+                                                             long long wait_cycles, long long drop_item) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
       if (lane == 0) {
         const long long t0 = clock64();
         while (*claim_turn != k) {
-          if (clock64() - t0 > kWaitCycles) { atomicExch(status, kStatusTimeout); ok = false; break; }
+          if (clock64() - t0 > wait_cycles) { atomicExch(status, kStatusTimeout); ok = false; break; }
           __nanosleep(64);
         }
         if (ok) {
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
       // stores of that item are then ordered before this warp's release of
       // the item's step counter (the fence waits here, not in the consumers)
       if (use > 0) {
-        if (lane == 0) ok = mbar_wait_backoff(&empty[st], (uint32_t)((use - 1) & 1), status, 128);
+        if (lane == 0) ok = mbar_wait_backoff(&empty[st], (uint32_t)((use - 1) & 1), status, 128, wait_cycles);
         if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
         if (lane == 0 && pj >= 0) st_release(jobs[pj].done + ptile, ps + 1);
       }
@@ -310,6 +317,23 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
         break;
       }
       const BatchJob& jb = jobs[j];
+      if (item == drop_item) {
+        // left out on purpose: the consumers skip it and its tile's step
+        // counter stays behind, so the items that need it wait until their
+        // limit runs out
+        pj = -1;
+        __syncwarp();
+        if (lane == 0) {
+          slot[st].job = j;
+          slot[st].s = s;
+          slot[st].tile = tile;
+          slot[st].end = 0;
+          slot[st].skip = 1;
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+        }
+        __syncwarp();
+        continue;
+      }
       // lanes 0..8 each wait for one tile of the 3 x 3 neighbourhood (step
       // s-1); after the release above, so a wait on this CTA's own item k - 2
       // cannot block its publication
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
           if (ld_acquire(flag) < s) {
             const long long t0 = clock64();
             while (ld_acquire(flag) < s) {
-              if (clock64() - t0 > kWaitCycles) { atomicExch(status, kStatusTimeout); break; }
+              if (clock64() - t0 > wait_cycles) { atomicExch(status, kStatusTimeout); break; }
               __nanosleep(128);
             }
           }
@@ -335,6 +359,7 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
         slot[st].s = s;
         slot[st].tile = tile;
         slot[st].end = 0;
+        slot[st].skip = 0;
         if (s > 0 || jb.tma0) {
           // the neighbours' generic-proxy stores must be visible to the TMA read
           asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -359,10 +384,15 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
   int cur_job = -1;
   for (long long k = 0;; ++k) {
     const int st = (int)(k & 1);
-    const bool landed = mbar_wait_backoff(&full[st], (uint32_t)((k >> 1) & 1), status, 32);
+    const bool landed = mbar_wait_backoff(&full[st], (uint32_t)((k >> 1) & 1), status, 32, wait_cycles);
     if (!landed) break;
     const ItemSlot it = slot[st];
     if (it.end) break;
+    if (it.skip) {
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+      continue;
+    }
     const BatchJob& jb = jobs[it.job];
     if (it.job != cur_job) {
       const int na = 2 * jb.r + 2;
@@ -411,9 +441,24 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
 
 using namespace spider;
 
+extern "C" spider_status spider_set_wait_limit(long long cycles) {
+  set_error("");
+  if (cycles < 1000) return fail(SPIDER_ERR_INVALID, "wait limit must be >= 1000 cycles");
+  set_wait_limit_cycles(cycles);
+  return SPIDER_OK;
+}
+
+extern "C" spider_status spider_batch_drop_item(long long item) {
+  set_error("");
+  if (item < -1) return fail(SPIDER_ERR_INVALID, "item must be >= -1");
+  g_drop_item.store(item);
+  return SPIDER_OK;
+}
+
 extern "C" spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                                       const int64_t* steps, cudaStream_t stream) {
   set_error("");
+  const long long drop_item = g_drop_item.exchange(-1);  // the hook applies to this call only
   if (n < 0 || n > 4096) return fail(SPIDER_ERR_INVALID, "n must be in [0, 4096]");
   if (n == 0) return SPIDER_OK;
   if (!plans || !ins || !outs || !steps) return fail(SPIDER_ERR_INVALID, "NULL array");
@@ -629,8 +674,11 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     int a_max = max_steps;
     int* a_ctr = reinterpret_cast<int*>(dev + o_ctr);
     int* a_status = reinterpret_cast<int*>(dev + o_status);
+    long long a_wait = wait_limit_cycles();
+    long long a_drop = drop_item;
     void* kargs[] = {(void*)&a_tables, (void*)&a_tbytes, (void*)&a_tsm, (void*)&a_oo, (void*)&a_os, (void*)&a_oa,
-                     (void*)&a_ot, (void*)&a_maps, (void*)&a_max, (void*)&a_ctr, (void*)&a_status};
+                     (void*)&a_ot, (void*)&a_maps, (void*)&a_max, (void*)&a_ctr, (void*)&a_status,
+                     (void*)&a_wait, (void*)&a_drop};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphCreate(&graph, 0);

@@ -1,10 +1,15 @@
 // Serving: continuous batching of stencil jobs on one GPU.
 //
 // spider_submit copies the job (plan parameters, host grid) into a FIFO queue.
-// A worker thread owns kSlots CUDA streams.  Each loop it
+// A worker thread owns kSlots CUDA streams and a stream-ordered memory pool
+// (cudaMemPool_t) that keeps up to the HBM budget reserved.  Each loop it
 //  * admits queued jobs in arrival order while a stream slot is free and the
 //    job's device memory (three grids: current, next, and the plan's scratch)
-//    fits the HBM budget next to the jobs already on the device;
+//    fits the HBM budget next to the jobs already on the device; a job's
+//    grids and its plan's buffers are allocated from the pool on the job's
+//    stream and returned to it there (cudaMallocFromPoolAsync /
+//    cudaFreeAsync), so admitting or finishing a job never waits for the
+//    device or for the other jobs' work;
 //  * advances every running job by one chunk of at most kChunkSteps time
 //    steps once its previous chunk has finished, so a job admitted while
 //    others run starts within one chunk and its kernels interleave with
@@ -12,8 +17,13 @@
 //  * copies finished results back, frees their memory and records the
 //    submit-to-completion latency.
 // A job's arithmetic does not depend on what else runs: the result is the
-// same as a lone spider_run of the same plan.
+// same as a lone spider_run of the same plan in the arithmetic chosen for
+// it.  The arithmetic is the fastest whose a priori error bound
+// (spider_plan_error_bound) meets the job's error target: sparse TF32, then
+// the FP16 hi/lo split, then FP32 on CUDA cores.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -38,6 +48,7 @@ using Clock = std::chrono::steady_clock;
 struct Job {
   uint64_t ticket = 0;
   spider_plan plan = nullptr;
+  double bound = 0;         // a priori error bound of the chosen arithmetic
   int64_t steps = 0, done_steps = 0;
   std::vector<float> host;  // input at submit, result when done
   float* cur = nullptr;
@@ -66,6 +77,7 @@ struct spider_server_t {
   bool stop = false;
   cudaStream_t streams[spider::kSlots] = {};
   bool slot_busy[spider::kSlots] = {};
+  cudaMemPool_t pool = nullptr;
   std::thread worker;
 };
 
@@ -81,8 +93,10 @@ size_t job_bytes(const spider_plan_t* p) {
 }
 
 void finish(spider_server_t* s, Job* j, spider_status st, const std::string& err) {
-  if (j->cur) cudaFree(j->cur);
-  if (j->nxt) cudaFree(j->nxt);
+  // stream-ordered frees: after the job's own work, without waiting for it
+  cudaStream_t js = j->slot >= 0 ? s->streams[j->slot] : nullptr;
+  if (j->cur) cudaFreeAsync(j->cur, js);
+  if (j->nxt) cudaFreeAsync(j->nxt, js);
   j->cur = j->nxt = nullptr;
   if (j->ev) cudaEventDestroy(j->ev);
   j->ev = nullptr;
@@ -125,19 +139,23 @@ bool admit(spider_server_t* s, Job* j) {
     if (!s->slot_busy[k]) { slot = k; break; }
   if (slot < 0 || s->used + j->reserve > s->budget) return false;
   const size_t bytes = j->host.size() * sizeof(float);
-  cudaError_t e = cudaMalloc(&j->cur, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&j->nxt, bytes);
+  cudaStream_t st = s->streams[slot];
+  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->cur), bytes, s->pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->nxt), bytes, s->pool, st);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (j->cur) cudaFree(j->cur);
-    if (j->nxt) cudaFree(j->nxt);
+    if (j->cur) cudaFreeAsync(j->cur, st);
+    if (j->nxt) cudaFreeAsync(j->nxt, st);
     j->cur = j->nxt = nullptr;
     return false;  // device memory is short right now: retry when a job finishes
   }
   s->slot_busy[slot] = true;
   j->slot = slot;
   s->used += j->reserve;
+  // the plan's own buffers come from the pool too, on the job's stream
+  j->plan->dev.pool = s->pool;
+  j->plan->dev.pool_stream = st;
   e = cudaMemcpyAsync(j->cur, j->host.data(), bytes, cudaMemcpyHostToDevice, s->streams[slot]);
   if (e != cudaSuccess) { finish(s, j, SPIDER_ERR_CUDA, cudaGetErrorString(e)); return true; }
   s->running.push_back(j);
@@ -198,6 +216,24 @@ spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out) 
       return fail(SPIDER_ERR_CUDA, "cudaStreamCreate");
     }
   }
+  // a pool of device memory that keeps what it has grown to (up to the
+  // budget) instead of returning it at every synchronisation
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  cudaError_t pe = cudaMemPoolCreate(&s->pool, &props);
+  if (pe == cudaSuccess) {
+    uint64_t keep = hbm_budget_bytes;
+    pe = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (pe != cudaSuccess) {
+    cudaGetLastError();
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    for (int k = 0; k < kSlots; ++k) cudaStreamDestroy(s->streams[k]);
+    delete s;
+    return fail(SPIDER_ERR_CUDA, std::string("memory pool: ") + cudaGetErrorString(pe));
+  }
   s->worker = std::thread(worker_loop, s);
   *out = s;
   return SPIDER_OK;
@@ -208,17 +244,44 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
   set_error("");
   if (!s || !plan || !host_in || !ticket || steps < 0 || !(err_target > 0))
     return fail(SPIDER_ERR_INVALID, "bad arguments");
-  // a private plan: split precision for tight error targets
-  // (the wide layout of radius 4..7 is TF32 only)
-  const spider_precision prec = (err_target <= 1e-4 && plan->r <= kMaxR) ? SPIDER_F16X2 : plan->prec;
+  // a private plan in the fastest arithmetic whose a priori error bound
+  // meets the target: sparse TF32 (the plan's precision and engine as
+  // given, when they meet it), the FP16 hi/lo split (|values| must stay below
+  // the FP16 range: the input's largest magnitude, the field not growing),
+  // then FP32 on CUDA cores
+  const int64_t npts = plan->points();
+  float amax = 0.f;
+  for (int64_t i = 0; i < npts; ++i) amax = std::max(amax, std::fabs(host_in[i]));
+  struct Choice { spider_precision prec; spider_engine engine; };
+  std::vector<Choice> choices = {{plan->prec, plan->engine}, {SPIDER_TF32, SPIDER_ENGINE_SPARSE_TC}};
+  if (amax < 16384.f) choices.push_back({SPIDER_F16X2, SPIDER_ENGINE_SPARSE_TC});
+  choices.push_back({SPIDER_TF32, SPIDER_ENGINE_CUDA_CORE});
+  int pick = -1;
+  double bound = 0;
+  for (size_t k = 0; k < choices.size() && pick < 0; ++k) {
+    const ErrorModel m = error_model(plan, choices[k].prec, choices[k].engine);
+    if (!m.built) continue;
+    bound = (double)steps * (m.wsum + m.drift) + m.floor;
+    if (bound <= err_target) pick = (int)k;
+  }
+  if (pick < 0)
+    return fail(SPIDER_ERR_UNSUPPORTED, "no arithmetic built for this stencil meets the error target");
   spider_plan copy = nullptr;
-  spider_status st = spider_plan_create(plan->ndim, plan->extents, plan->shape, plan->r, plan->w.data(), prec, &copy);
+  spider_status st = spider_plan_create(plan->ndim, plan->extents, plan->shape, plan->r, plan->w.data(),
+                                        choices[pick].prec, &copy);
   if (st != SPIDER_OK) return st;
-  if (plan->engine != SPIDER_ENGINE_SPARSE_TC) spider_plan_set_engine(copy, plan->engine);
+  if (choices[pick].engine != SPIDER_ENGINE_SPARSE_TC) {
+    st = spider_plan_set_engine(copy, choices[pick].engine);
+    if (st != SPIDER_OK) {
+      spider_plan_destroy(copy);
+      return st;
+    }
+  }
   copy->steps_per_pass = std::min(plan->steps_per_pass, max_steps_per_pass(copy));
   copy->tile_variant = plan->tile_variant;
   auto j = std::make_unique<Job>();
   j->plan = copy;
+  j->bound = bound;
   j->steps = steps;
   j->reserve = job_bytes(copy);
   if (j->reserve > s->budget) {
@@ -268,7 +331,11 @@ void spider_server_destroy(spider_server s) {
     s->cv.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  for (int k = 0; k < kSlots; ++k) cudaStreamDestroy(s->streams[k]);
+  for (int k = 0; k < kSlots; ++k) {
+    cudaStreamSynchronize(s->streams[k]);  // the stream-ordered frees have run
+    cudaStreamDestroy(s->streams[k]);
+  }
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
 }
 

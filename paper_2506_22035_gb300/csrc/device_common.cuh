@@ -13,9 +13,6 @@ namespace spider {
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 1;
 
-// A bounded wait gives up after this many SM clock cycles (~2 s at 2 GHz).
-constexpr long long kWaitCycles = 4000000000LL;
-
 // Programmatic dependent launch: a kernel launched with the programmatic
 // stream-serialization attribute may start while the previous kernel in the
 // stream finishes; it must wait here before touching any grid the previous
@@ -60,12 +57,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for phase `parity` of the barrier; returns false (and records a
-// timeout in *status) if it has not completed within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+// timeout in *status) if it has not completed within `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(status, kStatusTimeout);
       return false;
     }

@@ -26,11 +26,12 @@
 
 namespace spider {
 
-template <int R_, int T_, int BY_, int BX_, int H_, int NW_, int MINB_ = 1, int INS_ = 1>
+template <int R_, int T_, int BY_, int BX_, int H_, int NW_, int MINB_ = 1, int INS_ = 1, int VEC_ = 0>
 struct FuseCfg {
   static constexpr int RZ = 0, RY = R_, RX = R_, T = T_, BY = BY_, BX = BX_, H = H_, NW = NW_;
   static constexpr int kMinBlocks = MINB_;  // CTAs per SM the register budget must allow
   static constexpr int kInStages = INS_;    // input boxes in flight: 1, or 2 (prefetch a whole tile ahead)
+  static constexpr bool kVecStore = VEC_ != 0;  // final level: 16-byte stores after a quad transpose
   static constexpr int NA = 2 * RY + 2;
   static constexpr int kThreads = NW * 32;
   // level t: 0 = input box, T = output tile
@@ -54,6 +55,23 @@ struct FuseCfg {
 };
 
 __device__ __forceinline__ int swz(int col) { return col ^ (((col >> 5) & 1) << 3); }
+
+// 4 x 4 transpose across the four lanes of a warp that share q and have
+// g = 4a .. 4a + 3 (lanes 4 apart; i = g mod 4).  Lane i holds v_c for the
+// four (row, segment) combinations c of its output g; afterwards it holds,
+// for combination i, the outputs of the four lanes in order (four consecutive
+// x positions).  Two butterfly rounds of two shuffles each.
+__device__ __forceinline__ void quad_transpose(float& v0, float& v1, float& v2, float& v3, int i) {
+  const bool b0 = (i & 1) != 0, b1 = (i & 2) != 0;
+  float t0 = b0 ? v0 : v1, t1 = b0 ? v2 : v3;
+  t0 = __shfl_xor_sync(0xffffffffu, t0, 4);
+  t1 = __shfl_xor_sync(0xffffffffu, t1, 4);
+  if (b0) { v0 = t0; v2 = t1; } else { v1 = t0; v3 = t1; }
+  float u0 = b1 ? v0 : v2, u1 = b1 ? v1 : v3;
+  u0 = __shfl_xor_sync(0xffffffffu, u0, 8);
+  u1 = __shfl_xor_sync(0xffffffffu, u1, 8);
+  if (b1) { v0 = u0; v1 = u1; } else { v2 = u0; v3 = u1; }
+}
 
 struct FusedCtx {
   const StepArgs* args;
@@ -140,14 +158,14 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
       // level 1 reads the input grid, rounded already when RIN is false
       if (MODE == Mode::SpTF32) plane_sp_tf32<F, SP, LV == 1 && RIN>(row0, A, E, acc);
       else if (MODE == Mode::DenseTF32) plane_dense_tf32<F, SP, LV == 1 && RIN>(row0, Ad, acc);
-      else if (MODE == Mode::SpF16x2) plane_sp_split<F, false, SP>(row0, Am, Em, A, E, acc, accC);
-      else plane_sp_split<F, true, SP>(row0, Am, Em, A, E, acc, acc);
-      if (MODE == Mode::SpF16x2) {
-#pragma unroll
-        for (int i = 0; i < F::H / 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
+      else if (MODE == Mode::SpF16x2) plane_sp_split<F, false, 0, SP>(row0, Am, Em, A, E, acc, accC);
+      else {
+        // BF16 hi/mid/lo: two passes, each with its own operands
+        uint4 Am2[F::RY + 1], A2[F::NA];
+        uint32_t Em2[F::RY + 1], E2[F::NA];
+        plane_split<F, MODE, SP>(args, 0, c.lane, row0, Am2, Em2, A2, E2, acc, accC);
       }
+      if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) combine_split<MODE>(acc, accC);
       constexpr bool kStoreTF32 = (MODE == Mode::SpTF32 || MODE == Mode::DenseTF32);
       const int gy0 = c.y0 - GY + r0, gx0 = c.x0 - GX + 8 * s0;  // unit origin in the grid
       const bool interior = gy0 >= 0 && gy0 + F::H <= (int)args.ny && gx0 >= 0 && gx0 + 64 <= (int)args.nx;
@@ -186,7 +204,21 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
         if (kStoreTF32 && args.out_tf32) round_tf32_inplace(acc);
         float* o = args.dst + (int64_t)gy0 * args.pitch + gx0 + lx;
         const int pitch = (int)args.pitch;
-        if (interior) {
+        // 16-byte stores need rows that start on 16-byte boundaries
+        const bool vec = F::kVecStore && (args.pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(args.dst) & 15) == 0;
+        if (interior && vec) {
+          // lane (g, q) holds output g of segments 2q, 2q + 1 in rows 2pp,
+          // 2pp + 1; after the transpose lane i = g mod 4 holds combination
+          // i (row 2pp + i / 2, segment 2q + i mod 2) at x = 4 (g / 4) .. + 3
+          const int i = c.g & 3;
+          float* ob = args.dst + (int64_t)gy0 * args.pitch + gx0 + 16 * c.q + 8 * (i & 1) + (c.g & 4);
+#pragma unroll
+          for (int pp = 0; pp < F::H / 2; ++pp) {
+            float v0 = acc[pp][0], v1 = acc[pp][1], v2 = acc[pp][2], v3 = acc[pp][3];
+            quad_transpose(v0, v1, v2, v3, i);
+            *reinterpret_cast<float4*>(ob + (int64_t)(2 * pp + (i >> 1)) * pitch) = make_float4(v0, v1, v2, v3);
+          }
+        } else if (interior) {
 #pragma unroll
           for (int pp = 0; pp < F::H / 2; ++pp)
 #pragma unroll
@@ -282,7 +314,7 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
   }
 
   constexpr int NA = F::NA;
-  constexpr int CPP = (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) ? (F::RY + 1) + NA : NA;
+  constexpr int CPP = MODE == Mode::SpF16x2 ? (F::RY + 1) + NA : NA;
   uint4 A[NA];
   uint32_t E[NA];
   uint4 Ad[NA][2];
@@ -301,17 +333,10 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
       Ad[a][0] = args.a_words[((size_t)a * 32 + c.lane) * 2 + 0];
       Ad[a][1] = args.a_words[((size_t)a * 32 + c.lane) * 2 + 1];
     }
-  } else if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) {
-#pragma unroll
-    for (int k = 0; k <= F::RY; ++k) {
-      Am[k] = args.a_words[(size_t)k * 32 + c.lane];
-      Em[k] = args.meta[(size_t)k * 32 + c.lane];
-    }
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      A[a] = args.a_words[(size_t)(F::RY + 1 + a) * 32 + c.lane];
-      E[a] = args.meta[(size_t)(F::RY + 1 + a) * 32 + c.lane];
-    }
+  } else if (MODE == Mode::SpF16x2) {
+    load_split_operands<F>(args, 0, c.lane, Am, Em, A, E);
+  } else if (MODE == Mode::SpBF16x3) {
+    // two passes of operands, loaded per warp unit (see fused_level)
   } else {
 #pragma unroll
     for (int i = 0; i < (2 * F::RY + 1) * (2 * F::RX + 1); ++i) W[i] = args.w[i];
@@ -322,10 +347,10 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int st = it % NS;
     const uint32_t parity = (uint32_t)((it / NS) & 1);
-    const bool ok = mbar_wait_bounded(&bar[st], parity, args.status);
+    const bool ok = mbar_wait_bounded(&bar[st], parity, args.status, args.wait_cycles);
     if (!__syncthreads_and(ok)) {
       // the load we gave up on may still land: wait for it once more (bounded)
-      if (tid == 0) (void)mbar_wait_bounded(&bar[st], parity, args.status);
+      if (tid == 0) (void)mbar_wait_bounded(&bar[st], parity, args.status, args.wait_cycles);
       break;
     }
     c.x0 = (t % args.tiles_x) * F::BX;

@@ -1,6 +1,7 @@
 // Dispatch of one stencil step to the kernel of the plan's engine/precision,
 // and TMA tensor-map encoding through the driver entry point (no link-time
 // dependency on libcuda).
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -51,6 +52,14 @@ bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, in
   return r == CUDA_SUCCESS;
 }
 
+namespace {
+std::atomic<long long> g_wait_cycles{kDefaultWaitCycles};
+}
+
+long long wait_limit_cycles() { return g_wait_cycles.load(std::memory_order_relaxed); }
+
+void set_wait_limit_cycles(long long cycles) { g_wait_cycles.store(cycles, std::memory_order_relaxed); }
+
 int device_sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -65,6 +74,7 @@ cudaError_t launch_step(const LaunchCtx& ctx) {
   switch (p->engine) {
     case SPIDER_ENGINE_CUDA_CORE: return launch_cuda_core(cls, p->r, ctx);
     case SPIDER_ENGINE_DENSE_TC: return launch_dense_tf32(cls, p->r, ctx);
+    case SPIDER_ENGINE_SPARSE_TC_COPY: return launch_sp_tf32_copy(cls, p->r, ctx);
     default: break;
   }
   switch (p->prec) {
@@ -81,6 +91,7 @@ namespace spider {
 cudaError_t launch_pass(const LaunchCtx& ctx, int T) {
   if (T <= 1) return launch_step(ctx);
   const spider_plan_t* p = ctx.plan;
+  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY) return cudaErrorNotSupported;
   if (p->ndim == 1) return p->wide() ? launch_wide1d_fused_sp_tf32(p->r, T, ctx) : cudaErrorNotSupported;
   if (p->ndim == 3) {
     if (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3)

@@ -37,6 +37,8 @@ cudaError_t launch_sp_f16x2(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_sp_bf16x3(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_dense_tf32(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_cuda_core(int cls, int r, const LaunchCtx& ctx);
+// SPIDER_ENGINE_SPARSE_TC_COPY: the explicit row-swap copy (2-D only).
+cudaError_t launch_sp_tf32_copy(int cls, int r, const LaunchCtx& ctx);
 // Radius 4..7 (1-D and 2-D), sparse TF32, wide layout.
 cudaError_t launch_wide_sp_tf32(int cls, int r, const LaunchCtx& ctx);
 // Fused passes of T = 2..4 steps for 1-D sparse TF32 plans (wide layout,
@@ -75,5 +77,8 @@ bool make_tensor_map_pitched(CUtensorMap* map, const float* base, int64_t nx, in
                              int box_x, int box_y, int box_z);
 
 int device_sm_count();
+
+// Limit of the kernels' bounded waits in SM cycles (spider_set_wait_limit).
+long long wait_limit_cycles();
 
 }  // namespace spider

@@ -58,10 +58,10 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   {
     std::lock_guard<std::mutex> lock(mu);
     if (occ_by_dev[dev] == 0) {
-      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_bytes<C, MODE>());
       if (err != cudaSuccess) return err;
       int o = 0;
-      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, C::kSmemBytes);
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::kThreads, step_smem_bytes<C, MODE>());
       if (err != cudaSuccess) return err;
       occ_by_dev[dev] = std::max(o, 1);
     }
@@ -81,6 +81,7 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   a.use_tma = make_src_map(&map, ctx, p->nz, C::SX, C::SY, C::SZ) ? 1 : 0;
@@ -89,7 +90,7 @@ cudaError_t launch_cfg_k(const LaunchCtx& ctx) {
   const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z;
   if (ntiles > (1LL << 31) - 1) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(ntiles, (long long)occ * ctx.sms);
-  return launch_pdl(kern, grid, C::kThreads, C::kSmemBytes, ctx.stream, map, a);
+  return launch_pdl(kern, grid, C::kThreads, step_smem_bytes<C, MODE>(), ctx.stream, map, a);
 }
 
 // TF32 modes read a grid stored already rounded (ctx.in_tf32) with the
@@ -166,6 +167,7 @@ cudaError_t launch_stream3d_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.use_tma = 1;
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ncol = (long long)a.tiles_x * a.tiles_y;
@@ -272,6 +274,7 @@ cudaError_t launch_fused_cfg_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.use_tma = 1;
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ntiles = (long long)a.tiles_x * a.tiles_y;
@@ -294,15 +297,15 @@ cudaError_t launch_fused_cfg(const LaunchCtx& ctx) {
 //   0: H = 8,  two input boxes in flight      1: H = 16, two input boxes
 //   2: H = 8,  one input box, registers capped for 3 CTAs per SM
 //   3: H = 16, one input box
-template <int R, int T, int H, int MINB, int INS, int L1 = 64>
-using FusedTile = FuseCfg<R, T, L1 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB, INS>;
+template <int R, int T, int H, int MINB, int INS, int L1 = 64, int VEC = 0>
+using FusedTile = FuseCfg<R, T, L1 - 2 * R * (T - 1), 8 * (17 - T), H, 8, MINB, INS, VEC>;
 
-template <Mode MODE, int R, int H, int MINB, int INS, int L1 = 64>
+template <Mode MODE, int R, int H, int MINB, int INS, int L1 = 64, int VEC = 0>
 cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
   switch (T) {
-    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB, INS, L1>, MODE>(ctx);
-    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB, INS, L1>, MODE>(ctx);
-    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB, INS, L1>, MODE>(ctx);
+    case 2: return launch_fused_cfg<FusedTile<R, 2, H, MINB, INS, L1, VEC>, MODE>(ctx);
+    case 3: return launch_fused_cfg<FusedTile<R, 3, H, MINB, INS, L1, VEC>, MODE>(ctx);
+    case 4: return launch_fused_cfg<FusedTile<R, 4, H, MINB, INS, L1, VEC>, MODE>(ctx);
     default: return cudaErrorNotSupported;
   }
 }
@@ -315,18 +318,22 @@ cudaError_t launch_fused_rh(int T, const LaunchCtx& ctx) {
 // in registers): 2 and 3 run as 0 and 1.  Variant 4 is the small tile: level
 // 1 of 32 rows, one warp unit per warp per level, four times the tiles of
 // the 64-row shapes -- for grids too small to fill the GPU, where a pass is
-// the latency of one tile's levels.
+// the latency of one tile's levels.  Variant 5 (sparse TF32): variant 2 with
+// the final level written by 16-byte stores after a transpose of the
+// accumulator fragments within groups of four lanes (other modes: as 2).
 template <Mode MODE, int R>
 cudaError_t launch_fused_r(int T, const LaunchCtx& ctx) {
   int v = ctx.plan->tile_variant;
   if (v == 4) return launch_fused_rh<MODE, R, 8, 1, 2, 32>(T, ctx);
   if constexpr (MODE == Mode::SpTF32) {
+    if (v == 5) return launch_fused_rh<MODE, R, 8, 3, 1, 64, 1>(T, ctx);
     if (v == 2) return launch_fused_rh<MODE, R, 8, 3, 1>(T, ctx);
     if (v == 3) return launch_fused_rh<MODE, R, 16, 1, 1>(T, ctx);
   } else if constexpr (MODE != Mode::CudaCore) {
-    if (v == 2) return launch_fused_rh<MODE, R, 8, 2, 2>(T, ctx);
+    if (v == 2 || v == 5) return launch_fused_rh<MODE, R, 8, 2, 2>(T, ctx);
     if (v == 3) return launch_fused_rh<MODE, R, 8, 2, 1>(T, ctx);
   } else {
+    if (v == 5) v = 2;
     if (v >= 2) v -= 2;
   }
   return v == 1 ? launch_fused_rh<MODE, R, 16, 1, 2>(T, ctx) : launch_fused_rh<MODE, R, 8, 1, 2>(T, ctx);
@@ -407,6 +414,7 @@ cudaError_t launch_fused3d_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.use_tma = 1;
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const long long ncol = (long long)a.tiles_x * a.tiles_y;
@@ -447,7 +455,7 @@ cudaError_t launch_fused3d_cfg(const LaunchCtx& ctx) {
 template <Mode MODE, int T>
 cudaError_t launch_fused3d_t(const LaunchCtx& ctx) {
   constexpr int kMinB = T == 4 ? 1 : 2;
-  const int v = ctx.plan->tile_variant;
+  const int v = ctx.plan->tile_variant == 5 ? 2 : ctx.plan->tile_variant;
   if (v % 2 == 1) return launch_fused3d_cfg<Fuse3Cfg<1, T, 32, 8, 8, 1>, MODE>(ctx);
   if (T == 2 && v == 2) return launch_fused3d_cfg<Fuse3Cfg<1, T, 16, 4, 8, 3>, MODE>(ctx);
   return launch_fused3d_cfg<Fuse3Cfg<1, T, 16, 4, 8, kMinB>, MODE>(ctx);
@@ -503,6 +511,7 @@ cudaError_t launch_wide_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
@@ -553,6 +562,7 @@ cudaError_t launch_wide1d_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
@@ -609,6 +619,7 @@ cudaError_t launch_wide1d_fused_k(const LaunchCtx& ctx) {
   a.meta = p->dev.meta_words;
   a.w = p->dev.w_dense;
   a.status = p->dev.status;
+  a.wait_cycles = wait_limit_cycles();
   a.use_tma = 1;
   a.out_tf32 = ctx.out_tf32 ? 1 : 0;
   const int grid = (int)std::min<long long>(a.tiles_x, (long long)occ * ctx.sms);

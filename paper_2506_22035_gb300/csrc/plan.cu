@@ -68,30 +68,20 @@ static float bf_value(float x) { return __bfloat162float(__float2bfloat16_rn(x))
 
 int combos_per_plane(spider_precision prec, int ry) {
   switch (prec) {
-    case SPIDER_F16X2:
-    case SPIDER_BF16X3:
-      return (ry + 1) + (2 * ry + 2);
-    default:
-      return 2 * ry + 2;
+    case SPIDER_F16X2: return (ry + 1) + (2 * ry + 2);
+    case SPIDER_BF16X3: return 2 * ((ry + 1) + (2 * ry + 2));
+    default: return 2 * ry + 2;
   }
 }
 
 namespace {
 
-// Which part of a coefficient an operand carries.
-enum class Part { Full, TF32, F16Hi, F16LoScaled, BF16Hi, BF16Lo };
+// Which part of a coefficient an operand carries: the coefficient itself
+// (the cube passed in is then already the part wanted, e.g. the TF32
+// rounding or one term of a split).
+enum class Part { Full };
 
-float part_value(float w, Part part) {
-  switch (part) {
-    case Part::Full: return w;
-    case Part::TF32: return tf32_value(w);
-    case Part::F16Hi: return h_value(w);
-    case Part::F16LoScaled: return h_value((w - h_value(w)) * 2048.0f);
-    case Part::BF16Hi: return bf_value(w);
-    case Part::BF16Lo: return bf_value(w - bf_value(w));
-  }
-  return 0.f;
-}
+float part_value(float w, Part) { return w; }
 
 struct WindowMatrix {
   float v[16][16];
@@ -144,6 +134,112 @@ std::vector<float> tf32_sum_preserving(const std::vector<float>& w) {
   }
   return out;
 }
+
+// The two 16-bit neighbours of x (FP16 or BF16): *near is x rounded to
+// nearest, *far the neighbour on the other side of x (equal to *near when x
+// is exactly representable, or when the step would leave the finite range).
+void neighbours16(float x, bool bf16, float* near, float* far) {
+  const uint16_t b = bf16 ? bf_bits(x) : h_bits(x);
+  auto value = [&](uint16_t u) {
+    if (bf16) {
+      const uint32_t f = (uint32_t)u << 16;
+      float v;
+      std::memcpy(&v, &f, 4);
+      return v;
+    }
+    __half h;
+    std::memcpy(&h, &u, 2);
+    return __half2float(h);
+  };
+  *near = value(b);
+  *far = *near;
+  if (*near == x) return;
+  const uint16_t sign = b & 0x8000u, mag = b & 0x7FFFu;
+  const uint16_t inf = bf16 ? 0x7F80u : 0x7C00u;
+  uint16_t m2;
+  if (std::fabs(*near) < std::fabs(x)) {
+    m2 = (uint16_t)(mag + 1);
+    if (m2 >= inf) return;
+  } else {
+    m2 = (uint16_t)(mag - 1);  // |near| > |x| >= 0, so mag >= 1
+  }
+  *far = value((uint16_t)(sign | m2));
+}
+
+// Greedy flips that bring sum_i (need_i - scale * out_i) as close to zero as
+// possible, each out_i taking one of its two candidates (out_i, other_i).
+// The rule of tf32_sum_preserving, for the last term of a split.
+void sum_preserving_flips(const std::vector<double>& need, std::vector<float>& out, std::vector<float>& other,
+                          double scale) {
+  const size_t n = out.size();
+  double resid = 0;
+  for (size_t i = 0; i < n; ++i) resid += need[i] - scale * (double)out[i];
+  std::vector<bool> flipped(n, false);
+  for (;;) {
+    int best = -1;
+    double best_abs = std::fabs(resid), best_cost = 0;
+    for (size_t i = 0; i < n; ++i) {
+      if (flipped[i] || other[i] == out[i]) continue;
+      const double delta = scale * ((double)other[i] - (double)out[i]);
+      const double r2 = std::fabs(resid - delta);
+      const double cost = std::fabs(need[i] - scale * (double)other[i]);
+      if (r2 < best_abs || (best >= 0 && r2 == best_abs && cost < best_cost)) {
+        best = (int)i;
+        best_abs = r2;
+        best_cost = cost;
+      }
+    }
+    if (best < 0) break;
+    resid -= scale * ((double)other[best] - (double)out[best]);
+    std::swap(out[best], other[best]);
+    flipped[best] = true;
+  }
+}
+
+}  // namespace
+
+// Split weights (see spider_internal.h).  FP16: hi = w rounded to FP16,
+// lo = (w - hi) * 2^11 rounded to FP16.  BF16: hi, mid = (w - hi) and
+// lo = (w - hi - mid), each rounded to BF16; the differences are exact in
+// FP32.  The last term of every weight takes one of its two 16-bit
+// neighbours so that the split weights sum as close as possible to the FP32
+// weights: a rounding error of the sum multiplies the constant mode every
+// step and grows linearly with the step count, where the rounding errors of
+// single weights do not.
+SplitWeights split_weights(const std::vector<float>& w, spider_precision prec) {
+  SplitWeights sw;
+  const size_t n = w.size();
+  const bool bf = prec == SPIDER_BF16X3;
+  sw.hi.resize(n);
+  sw.mid.assign(n, 0.f);
+  sw.lo.resize(n);
+  sw.lo_scale = bf ? 1.0 : 1.0 / 2048.0;
+  std::vector<float> other(n);
+  std::vector<double> need(n);
+  for (size_t i = 0; i < n; ++i) {
+    sw.hi[i] = bf ? bf_value(w[i]) : h_value(w[i]);
+    float rest = w[i] - sw.hi[i];
+    if (bf) {
+      sw.mid[i] = bf_value(rest);
+      rest = rest - sw.mid[i];
+    } else {
+      rest = rest * 2048.0f;
+    }
+    neighbours16(rest, bf, &sw.lo[i], &other[i]);
+    need[i] = (double)w[i] - (double)sw.hi[i] - (double)sw.mid[i];
+  }
+  sum_preserving_flips(need, sw.lo, other, sw.lo_scale);
+  return sw;
+}
+
+double split_sum_error(const std::vector<float>& w, const SplitWeights& sw) {
+  double d = 0;
+  for (size_t i = 0; i < w.size(); ++i)
+    d += (double)w[i] - ((double)sw.hi[i] + (double)sw.mid[i] + sw.lo_scale * (double)sw.lo[i]);
+  return d;
+}
+
+namespace {
 
 // A_a for plane dz (index dzi = dz + rz) in window coordinates; `coeffs`
 // supplies the cube (the plan's FP32 weights or their TF32 rounding).
@@ -316,6 +412,18 @@ spider_status build_operands(spider_plan_t* p) {
   p->meta_words.clear();
   try {
     const std::vector<float> w_tf32 = tf32_sum_preserving(p->w);
+    // weight-sum errors of every arithmetic, relative to sum |w| (the error
+    // model of spider_plan_error_bound)
+    double wabs = 0, d_tf32 = 0;
+    for (size_t i = 0; i < p->w.size(); ++i) {
+      wabs += std::fabs((double)p->w[i]);
+      d_tf32 += (double)p->w[i] - (double)w_tf32[i];
+    }
+    const double scale = wabs > 0 ? 1.0 / wabs : 0.0;
+    p->wsum_rel[0] = std::fabs(d_tf32) * scale;
+    p->wsum_rel[1] = std::fabs(split_sum_error(p->w, split_weights(p->w, SPIDER_F16X2))) * scale;
+    p->wsum_rel[2] = std::fabs(split_sum_error(p->w, split_weights(p->w, SPIDER_BF16X3))) * scale;
+    if (p->prec == SPIDER_F16X2 || p->prec == SPIDER_BF16X3) p->split = split_weights(p->w, p->prec);
     if (p->wide()) {
       // wide layout: [kernel row][K half][lane] (sparse TF32 only)
       const int nkr = 2 * p->ry + 1;
@@ -352,20 +460,30 @@ spider_status build_operands(spider_plan_t* p) {
           pack_tf32_sparse(window_matrix(p, w_tf32, dzi, a, Part::Full), &p->a_words[c * 128], &p->meta_words[c * 32]);
         }
       } else {
+        // One pass of combos per split term pair, each (ry + 1) two-row
+        // combos [K_x(2c) | K_x(2c+1)] x [X_x(j); X_x(j+1)] followed by na
+        // one-row combos [K_hi(a) | K_y(a)] x [X_y(j); X_hi(j)]:
+        //   FP16 hi/lo:      x = hi,  y = lo (scaled by 2^11)
+        //   BF16 hi/mid/lo:  pass 0 x = hi, y = mid; pass 1 x = mid, y = lo
         const bool bf = p->prec == SPIDER_BF16X3;
-        const Part hi = bf ? Part::BF16Hi : Part::F16Hi;
-        const Part lo = bf ? Part::BF16Lo : Part::F16LoScaled;
-        // main combos: [K_hi(2c) | K_hi(2c+1)] times [X_hi(j); X_hi(j+1)]
-        for (int c = 0; c <= p->ry; ++c) {
-          const size_t ci = (size_t)dzi * cpp + c;
-          pack_16bit_sparse_k32(window_matrix(p, p->w, dzi, 2 * c, hi), window_matrix(p, p->w, dzi, 2 * c + 1, hi), bf,
-                                &p->a_words[ci * 128], &p->meta_words[ci * 32]);
-        }
-        // correction combos: [K_hi(a) | K_lo(a)] times [X_lo(j); X_hi(j)]
-        for (int a = 0; a < na; ++a) {
-          const size_t ci = (size_t)dzi * cpp + (p->ry + 1) + a;
-          pack_16bit_sparse_k32(window_matrix(p, p->w, dzi, a, hi), window_matrix(p, p->w, dzi, a, lo), bf,
-                                &p->a_words[ci * 128], &p->meta_words[ci * 32]);
+        const SplitWeights& sw = p->split;
+        const int npass = bf ? 2 : 1;
+        const int per_pass = (p->ry + 1) + na;
+        for (int pass = 0; pass < npass; ++pass) {
+          const std::vector<float>& two_row = pass == 0 ? sw.hi : sw.mid;
+          const std::vector<float>& cross = (bf && pass == 0) ? sw.mid : sw.lo;
+          for (int c = 0; c <= p->ry; ++c) {
+            const size_t ci = (size_t)dzi * cpp + pass * per_pass + c;
+            pack_16bit_sparse_k32(window_matrix(p, two_row, dzi, 2 * c, Part::Full),
+                                  window_matrix(p, two_row, dzi, 2 * c + 1, Part::Full), bf, &p->a_words[ci * 128],
+                                  &p->meta_words[ci * 32]);
+          }
+          for (int a = 0; a < na; ++a) {
+            const size_t ci = (size_t)dzi * cpp + pass * per_pass + (p->ry + 1) + a;
+            pack_16bit_sparse_k32(window_matrix(p, sw.hi, dzi, a, Part::Full),
+                                  window_matrix(p, cross, dzi, a, Part::Full), bf, &p->a_words[ci * 128],
+                                  &p->meta_words[ci * 32]);
+          }
         }
       }
     }

@@ -25,6 +25,10 @@ namespace spider {
 //    dy = j - y, the bottom half dy = j - y - 1, so one B fragment of input
 //    row j feeds both output rows and the accumulator never moves;
 //  * "A index" a = j - y + ry runs 0 .. 2ry+1 for each dz.
+// Default limit of the kernels' bounded waits: SM clock cycles (~2 s at 2 GHz).
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+void set_wait_limit_cycles(long long cycles);
+
 constexpr int kSeg = 8;          // L: outputs per segment
 constexpr int kWin = 16;         // 2L: input window per segment
 constexpr int kHaloX = 4;        // window starts 4 points left of the segment
@@ -82,6 +86,19 @@ struct DeviceState {
   float* host_stage_out = nullptr;
   int* status = nullptr;           // device error word (0 = ok)
   size_t scratch_bytes = 0;
+  // Stream-ordered allocation (the serving loop): when `pool` is set, every
+  // buffer above comes from it through cudaMallocFromPoolAsync on
+  // `pool_stream` and goes back through cudaFreeAsync on the same stream, so
+  // neither allocating nor freeing waits for the device.
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t pool_stream = nullptr;
+};
+
+// Split weights of the FP16 / BF16 precisions: w ~ hi + mid + lo_scale * lo
+// (FP16: mid = 0, lo scaled by 2^11; BF16: three BF16 terms).
+struct SplitWeights {
+  std::vector<float> hi, mid, lo;
+  double lo_scale = 1.0;
 };
 
 }  // namespace spider
@@ -102,6 +119,10 @@ struct spider_plan_t {
   int n_combos = 0;                      // A operands actually issued per dz-plane set
   std::vector<uint32_t> a_words;         // [combo][lane][4]  (dense TF32: [arow][lane][8])
   std::vector<uint32_t> meta_words;      // [combo][lane]
+  spider::SplitWeights split;            // FP16 / BF16 precisions
+  // |sum of the weights as the arithmetic holds them - sum of the FP32
+  // weights| / sum |w|, for TF32, FP16 hi/lo and BF16 hi/mid/lo
+  double wsum_rel[3] = {0, 0, 0};
   spider::DeviceState dev;
   std::mutex mu;
 
@@ -126,6 +147,11 @@ spider_status build_operands(spider_plan_t* p);
 uint32_t round_tf32_rna(float x);
 float tf32_value(float x);
 
+// plan.cu: the split weights of a 16-bit precision (sum-preserving last
+// term) and the error of their sum against the FP32 weights.
+SplitWeights split_weights(const std::vector<float>& w, spider_precision prec);
+double split_sum_error(const std::vector<float>& w, const SplitWeights& sw);
+
 // Number of A "combos" (register operands) for a precision, per dz plane.
 int combos_per_plane(spider_precision prec, int ry);
 
@@ -134,6 +160,13 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
 // api.cu: the largest number of time steps per HBM pass built for the plan
 // (fused kernels: 2-D stencils, and 3-D radius-1 stencils in sparse TF32).
 int max_steps_per_pass(const spider_plan_t* p);
+// api.cu: the a priori error model of an arithmetic for the plan's stencil
+// (spider_plan_error_bound): bound = steps * (wsum + drift) + floor.
+struct ErrorModel {
+  bool built = false;
+  double wsum = 0, drift = 0, floor = 0;
+};
+ErrorModel error_model(const spider_plan_t* p, spider_precision prec, spider_engine engine);
 // api.cu: upload the plan's operands (and allocate its scratch grid) if needed.
 spider_status ensure_plan_device(spider_plan_t* p, bool scratch);
 // autotune.cu: the tuned (steps per pass, tile variant) of the plan's kind

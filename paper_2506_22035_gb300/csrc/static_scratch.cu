@@ -3,9 +3,11 @@
 // spider_run allocates, on first use, the plan's device copy of its packed
 // operands and a scratch grid for ping-ponging between time steps.  This entry
 // point keeps both in file-scope __device__ arrays instead, so it never calls
-// cudaMalloc or cudaFree.  The arrays have fixed sizes, are shared by every
-// call in the process, and are held by every GPU that loads the library until
-// the process exits.
+// cudaMalloc or cudaFree.  It runs the same passes as spider_run (fused time
+// steps where the plan fuses) on grids TMA can read in their own layout.  The
+// arrays have fixed sizes, are shared by every call in the process, and are
+// held by every GPU that loads the library until the process exits.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -112,7 +114,8 @@ extern "C" spider_status spider_run_static(spider_plan p, const float* grid_in, 
   if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("operand upload: ") + cudaGetErrorString(e));
 
   // A stack view of the plan whose device state points at the static arrays;
-  // the launch code reads only its geometry, engine, precision and pointers.
+  // the launch code reads only its geometry, engine, precision, fusion depth,
+  // tile variant and pointers.
   spider_plan_t view;
   view.ndim = p->ndim;
   view.nx = p->nx;
@@ -125,6 +128,8 @@ extern "C" spider_status spider_run_static(spider_plan p, const float* grid_in, 
   view.shape = p->shape;
   view.prec = p->prec;
   view.engine = p->engine;
+  view.steps_per_pass = p->steps_per_pass;
+  view.tile_variant = p->tile_variant;
   view.dev.device = dev;
   view.dev.a_words = a.operands;
   view.dev.meta_words = a.meta;
@@ -132,18 +137,40 @@ extern "C" spider_status spider_run_static(spider_plan p, const float* grid_in, 
   view.dev.status = a.status;
   view.dev.scratch = a.scratch;
 
+  // The same passes as spider_run takes on grids TMA can read in their own
+  // layout: T fused steps per pass (the plan's setting), a single-step first
+  // pass when the input cannot be read through TMA, grids between passes
+  // stored rounded to TF32 in the TF32 engines.  Grids whose rows TMA cannot
+  // describe have no padded grids here: they run one step per pass.
+  auto aligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const int m = p->ndim == 1 ? 8 : 4;
+  const bool tma_out = p->nx % m == 0 && aligned(grid_out);
+  const bool tma_in = p->nx % m == 0 && aligned(grid_in);
+  const int T = tma_out ? std::min(p->steps_per_pass, max_steps_per_pass(p)) : 1;
+  const int head = (T > 1 && !tma_in) ? 1 : 0;
+  const int64_t body = steps - head;
+  const int64_t full = body / T;
+  const int rem = (int)(body % T);
+  const int64_t npasses = head + full + (rem ? 1 : 0);
+  const bool tf32 = tma_out && (p->engine == SPIDER_ENGINE_DENSE_TC || p->engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
+                                (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 &&
+                                 p->prec != SPIDER_BF16X3));
   LaunchCtx ctx;
   ctx.plan = &view;
   ctx.stream = stream;
   ctx.sms = device_sm_count();
   float* bufs[2] = {grid_out, a.scratch};
-  const int first = (steps % 2 == 1) ? 0 : 1;  // the last step lands in grid_out
-  for (int64_t t = 0; t < steps; ++t) {
-    ctx.dst = bufs[(first + t) % 2];
-    ctx.src = (t == 0) ? grid_in : bufs[(first + t - 1) % 2];
-    e = launch_step(ctx);
+  const int first = (npasses % 2 == 1) ? 0 : 1;  // the last pass lands in grid_out
+  for (int64_t k = 0; k < npasses; ++k) {
+    const bool last = k + 1 == npasses;
+    const int n = k < head ? 1 : (k - head < full ? T : rem);
+    ctx.dst = bufs[(first + k) % 2];
+    ctx.src = (k == 0) ? grid_in : bufs[(first + k - 1) % 2];
+    ctx.in_tf32 = tf32 && k > 0;
+    ctx.out_tf32 = tf32 && !last;
+    e = launch_pass(ctx, n);
     if (e == cudaErrorNotSupported) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil/engine");
-    if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("stencil step launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(SPIDER_ERR_CUDA, std::string("stencil pass launch: ") + cudaGetErrorString(e));
   }
   return SPIDER_OK;
 }

@@ -32,7 +32,9 @@
 
 namespace spider {
 
-enum class Mode : int { SpTF32 = 0, SpF16x2 = 1, SpBF16x3 = 2, DenseTF32 = 3, CudaCore = 4 };
+// SpTF32Copy: SpTF32 with the input row swap done by an explicit copy of
+// every window into a buffer of its own (the baseline of Sec. 3.2).
+enum class Mode : int { SpTF32 = 0, SpF16x2 = 1, SpBF16x3 = 2, DenseTF32 = 3, CudaCore = 4, SpTF32Copy = 5 };
 
 struct StepArgs {
   const float* src;        // source grid (generic loader only)
@@ -44,6 +46,7 @@ struct StepArgs {
   const uint32_t* meta;    // packed metadata
   const float* w;          // coefficient cube (CUDA-core mode), float32
   int* status;             // device status word
+  long long wait_cycles;   // limit of every bounded wait (SM cycles)
   int use_tma;             // 1: TMA tile loads from `tmap`; 0: cooperative loads from src
   int out_tf32;            // TF32 modes: store the outputs rounded to TF32 (the grid feeds another step)
 };
@@ -55,7 +58,22 @@ struct StepArgs {
 // results, at one rounding per stored point instead of one per operand
 // load (each input value is loaded about 2.75 times by overlapping windows
 // and warp tiles).
-__host__ __device__ constexpr bool is_tf32_mode(Mode m) { return m == Mode::SpTF32 || m == Mode::DenseTF32; }
+__host__ __device__ constexpr bool is_tf32_mode(Mode m) {
+  return m == Mode::SpTF32 || m == Mode::DenseTF32 || m == Mode::SpTF32Copy;
+}
+__host__ __device__ constexpr bool is_sp_tf32(Mode m) { return m == Mode::SpTF32 || m == Mode::SpTF32Copy; }
+
+// Shared memory of the one-step kernel: two input stages, barriers and, for
+// SpTF32Copy, the buffer of swapped windows (every row's BX / 8 windows of 16
+// points, twice the row: consecutive windows overlap by 8 points).
+template <class C, Mode MODE>
+__host__ __device__ constexpr int step_window_bytes() {
+  return MODE == Mode::SpTF32Copy ? C::SY * C::SZ * (C::BX / 8) * 16 * 4 : 0;
+}
+template <class C, Mode MODE>
+__host__ __device__ constexpr int step_smem_bytes() {
+  return C::kSmemBytes + step_window_bytes<C, MODE>();
+}
 
 template <int N>
 __device__ __forceinline__ void round_tf32_inplace(float (&acc)[N][4]) {
@@ -149,24 +167,53 @@ __device__ __forceinline__ void plane_dense_tf32_centre(const float* row0, const
   plane_dense_tf32<C, SP, ROUND, C::RY, C::RY + 1>(row0, A, acc);
 }
 
-// Split precisions (FP16 hi/lo with the lo parts scaled by 2^11, or BF16
-// hi/lo): value v = hi + lo.  Per pair of input rows (j, j+1) one k32 MMA
-// takes hi*hi for both rows, and per row one k32 MMA takes
-// hi(w)*lo(v) + lo(w)*hi(v).
-template <class C, bool BF16>
-__device__ __forceinline__ void split4(const float4& v, uint32_t (&hi)[2], uint32_t (&lo)[2]) {
-  if (BF16) {
-    hi[0] = pack_bf162(v.x, v.y);
-    hi[1] = pack_bf162(v.z, v.w);
-    const float2 h01 = unpack_bf162(hi[0]), h23 = unpack_bf162(hi[1]);
-    lo[0] = pack_bf162(v.x - h01.x, v.y - h01.y);
-    lo[1] = pack_bf162(v.z - h23.x, v.w - h23.y);
-  } else {
+// Split precisions.  FP16 hi/lo: v = hi + lo * 2^-11 (lo scaled by 2^11);
+// BF16 hi/mid/lo: v = hi + mid + lo, 24 significant bits.  The products kept
+// are those above 2^-24 relative: FP16 hi*hi, hi*lo, lo*hi; BF16 hi*hi,
+// hi*mid, mid*hi, hi*lo, lo*hi, mid*mid.  They run in passes over the input
+// rows; pass P applies
+//  * per pair of input rows (j, j+1) one k32 MMA [K_x(a) | K_x(a+1)] x
+//    [X_x(j); X_x(j+1)] with x = hi in pass 0 (BF16 pass 1: x = mid);
+//  * per input row one k32 MMA [K_hi(a) | K_y(a)] x [X_y(j); X_hi(j)] with
+//    y = lo for FP16, y = mid in BF16 pass 0 and lo in pass 1.
+// The hi*hi products go to accM, each MMA into a fresh zero accumulator
+// that is then added in FP32: the tensor core adds a chain's products to its
+// running sum with fewer bits below the sum's leading digit than an FP32
+// add keeps, which shrinks the result by a few units in the last place per
+// step (measured: a relative error growing linearly with the step count on
+// fields of one sign); a fresh accumulator is the size of the products.
+// Everything else goes to accC, two to three orders of magnitude smaller.
+template <bool BF16, int PASS>
+__device__ __forceinline__ void split_terms(const float4& v, uint32_t (&two)[2], uint32_t (&cross)[2],
+                                            uint32_t (&hi)[2]) {
+  if (!BF16) {
     hi[0] = pack_half2(v.x, v.y);
     hi[1] = pack_half2(v.z, v.w);
     const float2 h01 = unpack_half2(hi[0]), h23 = unpack_half2(hi[1]);
-    lo[0] = pack_half2((v.x - h01.x) * 2048.0f, (v.y - h01.y) * 2048.0f);
-    lo[1] = pack_half2((v.z - h23.x) * 2048.0f, (v.w - h23.y) * 2048.0f);
+    cross[0] = pack_half2((v.x - h01.x) * 2048.0f, (v.y - h01.y) * 2048.0f);
+    cross[1] = pack_half2((v.z - h23.x) * 2048.0f, (v.w - h23.y) * 2048.0f);
+    two[0] = hi[0];
+    two[1] = hi[1];
+  } else {
+    hi[0] = pack_bf162(v.x, v.y);
+    hi[1] = pack_bf162(v.z, v.w);
+    const float2 h01 = unpack_bf162(hi[0]), h23 = unpack_bf162(hi[1]);
+    // v - hi is exact in FP32 (hi holds v's leading 8 bits), and so is
+    // v - hi - mid below
+    const float r0 = v.x - h01.x, r1 = v.y - h01.y, r2 = v.z - h23.x, r3 = v.w - h23.y;
+    uint32_t mid[2] = {pack_bf162(r0, r1), pack_bf162(r2, r3)};
+    if (PASS == 0) {
+      two[0] = hi[0];
+      two[1] = hi[1];
+      cross[0] = mid[0];
+      cross[1] = mid[1];
+    } else {
+      const float2 m01 = unpack_bf162(mid[0]), m23 = unpack_bf162(mid[1]);
+      two[0] = mid[0];
+      two[1] = mid[1];
+      cross[0] = pack_bf162(r0 - m01.x, r1 - m01.y);
+      cross[1] = pack_bf162(r2 - m23.x, r3 - m23.y);
+    }
   }
 }
 
@@ -177,32 +224,90 @@ __device__ __forceinline__ void mma_k32(float (&d)[4], const uint4& a, uint32_t 
   else mma_sp_f16_k32(d, a, e, b0, b1, b2, b3);
 }
 
-template <class C, bool BF16, int SP, int JJ>
+template <class C, bool BF16, int PASS, int SP, int JJ>
 __device__ __forceinline__ void sp_split_rows(uint32_t addr, const uint4 (&Am)[C::RY + 1],
                                               const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
                                               const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
                                               float (&accC)[C::H / 2][4]) {
-  uint32_t hi0[2], lo0[2], hi1[2], lo1[2];
-  split4<C, BF16>(lds128_at<JJ * SP * 4>(addr), hi0, lo0);
-  split4<C, BF16>(lds128_at<(JJ + 1) * SP * 4>(addr), hi1, lo1);
+  uint32_t t0[2], c0[2], h0[2], t1[2], c1[2], h1[2];
+  split_terms<BF16, PASS>(lds128_at<JJ * SP * 4>(addr), t0, c0, h0);
+  split_terms<BF16, PASS>(lds128_at<(JJ + 1) * SP * 4>(addr), t1, c1, h1);
 #pragma unroll
   for (int pp = 0; pp < C::H / 2; ++pp) {
     const int a0 = JJ - 2 * pp;  // even; rows JJ, JJ+1 use A indices a0, a0+1
     if (a0 >= 0 && a0 + 1 < C::NA) {
-      mma_k32<C, BF16>(accM[pp], Am[a0 / 2], Em[a0 / 2], hi0[0], hi0[1], hi1[0], hi1[1]);
-      mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], lo0[0], lo0[1], hi0[0], hi0[1]);
-      mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], lo1[0], lo1[1], hi1[0], hi1[1]);
+      if (PASS == 0) {
+        float f[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_k32<C, BF16>(f, Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) accM[pp][i] += f[i];
+      } else {
+        mma_k32<C, BF16>(accC[pp], Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
+      }
+      mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], c0[0], c0[1], h0[0], h0[1]);
+      mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], c1[0], c1[1], h1[0], h1[1]);
     }
   }
-  if constexpr (JJ + 2 < C::H + 2 * C::RY) sp_split_rows<C, BF16, SP, JJ + 2>(addr, Am, Em, Ac, Ec, accM, accC);
+  if constexpr (JJ + 2 < C::H + 2 * C::RY)
+    sp_split_rows<C, BF16, PASS, SP, JJ + 2>(addr, Am, Em, Ac, Ec, accM, accC);
 }
 
-template <class C, bool BF16, int SP = C::SX>
+template <class C, bool BF16, int PASS = 0, int SP = C::SX>
 __device__ __forceinline__ void plane_sp_split(const float* row0, const uint4 (&Am)[C::RY + 1],
                                                const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
                                                const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
                                                float (&accC)[C::H / 2][4]) {
-  sp_split_rows<C, BF16, SP, 0>(smem_u32(row0), Am, Em, Ac, Ec, accM, accC);
+  sp_split_rows<C, BF16, PASS, SP, 0>(smem_u32(row0), Am, Em, Ac, Ec, accM, accC);
+}
+
+// Packed combos of one pass of a split precision: (RY + 1) two-row combos,
+// then NA one-row combos, starting at combo `first`.
+template <class C>
+__device__ __forceinline__ void load_split_operands(const StepArgs& args, int first, int lane,
+                                                    uint4 (&Am)[C::RY + 1], uint32_t (&Em)[C::RY + 1],
+                                                    uint4 (&A)[C::NA], uint32_t (&E)[C::NA]) {
+#pragma unroll
+  for (int c = 0; c <= C::RY; ++c) {
+    Am[c] = args.a_words[(size_t)(first + c) * 32 + lane];
+    Em[c] = args.meta[(size_t)(first + c) * 32 + lane];
+  }
+#pragma unroll
+  for (int a = 0; a < C::NA; ++a) {
+    A[a] = args.a_words[(size_t)(first + C::RY + 1 + a) * 32 + lane];
+    E[a] = args.meta[(size_t)(first + C::RY + 1 + a) * 32 + lane];
+  }
+}
+
+// The whole split product of one dz plane (index dzi) into accM / accC:
+// FP16 one pass with the operands already in registers; BF16 two passes,
+// each loading its operands first.
+template <class C, Mode MODE, int SP = C::SX>
+__device__ __forceinline__ void plane_split(const StepArgs& args, int dzi, int lane, const float* row0,
+                                            uint4 (&Am)[C::RY + 1], uint32_t (&Em)[C::RY + 1], uint4 (&A)[C::NA],
+                                            uint32_t (&E)[C::NA], float (&accM)[C::H / 2][4],
+                                            float (&accC)[C::H / 2][4]) {
+  constexpr int kPass = (C::RY + 1) + C::NA;
+  if (MODE == Mode::SpF16x2) {
+    plane_sp_split<C, false, 0, SP>(row0, Am, Em, A, E, accM, accC);
+  } else {
+    // a loop the compiler keeps: one pass's operands live at a time
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      load_split_operands<C>(args, (2 * dzi + pass) * kPass, lane, Am, Em, A, E);
+      if (pass == 0) plane_sp_split<C, true, 0, SP>(row0, Am, Em, A, E, accM, accC);
+      else plane_sp_split<C, true, 1, SP>(row0, Am, Em, A, E, accM, accC);
+    }
+  }
+}
+
+// accM + accC with accC's scale: 2^-11 for FP16, 1 for BF16.
+template <Mode MODE, int N>
+__device__ __forceinline__ void combine_split(float (&accM)[N][4], const float (&accC)[N][4]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      accM[i][j] = MODE == Mode::SpF16x2 ? fmaf(accC[i][j], 1.0f / 2048.0f, accM[i][j]) : accM[i][j] + accC[i][j];
 }
 
 // --------------------------------------------------------------------------
@@ -254,7 +359,7 @@ __global__ void __launch_bounds__(C::kThreads)
 
   // Kernel-matrix operands resident in registers (2-D: for the whole kernel).
   constexpr int NA = C::NA;
-  constexpr int CPP = (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) ? (C::RY + 1) + NA : NA;
+  constexpr int CPP = MODE == Mode::SpF16x2 ? (C::RY + 1) + NA : NA;
   uint4 A[NA];
   uint32_t E[NA];
   uint4 Ad[NA][2];
@@ -262,7 +367,7 @@ __global__ void __launch_bounds__(C::kThreads)
   uint32_t Em[C::RY + 1];
   float W[(2 * C::RY + 1) * (2 * C::RX + 1)];
   auto load_operands = [&](int dzi) {
-    if (MODE == Mode::SpTF32) {
+    if (is_sp_tf32(MODE)) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;  // zero operands
@@ -276,17 +381,10 @@ __global__ void __launch_bounds__(C::kThreads)
         Ad[a][0] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 0];
         Ad[a][1] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 1];
       }
-    } else if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) {
-#pragma unroll
-      for (int c = 0; c <= C::RY; ++c) {
-        Am[c] = args.a_words[(size_t)(dzi * CPP + c) * 32 + lane];
-        Em[c] = args.meta[(size_t)(dzi * CPP + c) * 32 + lane];
-      }
-#pragma unroll
-      for (int a = 0; a < NA; ++a) {
-        A[a] = args.a_words[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
-        E[a] = args.meta[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
-      }
+    } else if (MODE == Mode::SpF16x2) {
+      load_split_operands<C>(args, dzi * CPP, lane, Am, Em, A, E);
+    } else if (MODE == Mode::SpBF16x3) {
+      // two passes of operands, loaded by plane_split
     } else {
       constexpr int NW = (2 * C::RY + 1) * (2 * C::RX + 1);
 #pragma unroll
@@ -302,7 +400,7 @@ __global__ void __launch_bounds__(C::kThreads)
     int x0, y0, z0;
     coords(t, x0, y0, z0);
     if (use_tma) {
-      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status, args.wait_cycles);
       if (!__syncthreads_and(ok)) break;
     } else {
       // Asynchronous copies (grids whose rows are not 16-byte aligned).
@@ -372,24 +470,36 @@ __global__ void __launch_bounds__(C::kThreads)
         const float* row0 = S + (size_t)(wz + dzi) * C::SY * C::SX + (size_t)(wy * C::H) * C::SX + wx * 64 +
                             8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
         const bool centre_only = STAR && dzi != C::RZ;
-        if (MODE == Mode::SpTF32) {
+        if (MODE == Mode::SpTF32Copy) {
+          // the explicit row-swap copy: every window of 16 input points (8
+          // apart, overlapping) goes to a buffer of its own in the order the
+          // MMA's K index wants, four 16-byte chunks per window with chunk c
+          // taken from window chunk sigma(c); the operands then load 16
+          // contiguous bytes per lane from it
+          constexpr int NSEG = C::BX / 8, WP = NSEG * 16;
+          float* Wb = reinterpret_cast<float*>(smem + 2 * C::kStageStride + 64);
+          const float* Sp = S + (size_t)(wz + dzi) * C::SY * C::SX;
+          for (int e = tid; e < C::SY * NSEG * 4; e += C::kThreads) {
+            const int row = e / (NSEG * 4), seg = (e / 4) % NSEG, cc = e % 4;
+            const int sig = (cc == 1) ? 2 : (cc == 2) ? 1 : cc;
+            *reinterpret_cast<float4*>(Wb + row * WP + seg * 16 + 4 * cc) =
+                *reinterpret_cast<const float4*>(Sp + row * C::SX + 8 * seg + 4 * sig);
+          }
+          __syncthreads();
+          const float* wrow0 = Wb + (wy * C::H) * WP + (wx * 8 + g) * 16 + 4 * q;
+          plane_sp_tf32<C, WP, RIN>(wrow0, A, E, acc);
+          __syncthreads();  // the buffer is rewritten for the next plane or tile
+        } else if (MODE == Mode::SpTF32) {
           if (centre_only) plane_sp_tf32_centre<C, C::SX, RIN>(row0, A, E, acc);
           else plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
         } else if (MODE == Mode::DenseTF32) {
           if (centre_only) plane_dense_tf32_centre<C, C::SX, RIN>(row0, Ad, acc);
           else plane_dense_tf32<C, C::SX, RIN>(row0, Ad, acc);
-        } else if (MODE == Mode::SpF16x2) {
-          plane_sp_split<C, false>(row0, Am, Em, A, E, acc, accC);
         } else {
-          plane_sp_split<C, true>(row0, Am, Em, A, E, acc, acc);
+          plane_split<C, MODE>(args, dzi, lane, row0, Am, Em, A, E, acc, accC);
         }
       }
-      if (MODE == Mode::SpF16x2) {
-#pragma unroll
-        for (int i = 0; i < C::H / 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
-      }
+      if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) combine_split<MODE>(acc, accC);
       if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
       if (z < args.nz) {
         float* o = args.dst + (z * args.ny + ybase) * args.pitch + xbase + 16 * q + g;
@@ -438,7 +548,7 @@ __global__ void __launch_bounds__(C::kThreads)
     for (int k = 0; k < 2; ++k) {
       const int t = blockIdx.x + (it + k) * gridDim.x;
       if (t < ntiles) {
-        (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+        (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status, args.wait_cycles);
       }
     }
   }

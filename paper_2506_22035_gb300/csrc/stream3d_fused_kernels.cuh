@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
     bool ok = true;
     for (int zi = c.zstart; zi <= c.zend; ++zi) {
       const int s = f3_slot0<C>(c, zi);
-      ok = ok && mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status);
+      ok = ok && mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status, args.wait_cycles);
       phases ^= 1u << s;
       pending &= ~(1u << s);
       if (!__syncthreads_and(ok)) break;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
       // loads still in flight after a wait ran out: wait for them (bounded)
       if (c.tid == 0)
         for (int s = 0; s < C::NP0; ++s)
-          if ((pending >> s) & 1) (void)mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status);
+          if ((pending >> s) & 1) (void)mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status, args.wait_cycles);
       break;
     }
     c.rot = (c.rot + (c.zend - c.zstart + 1)) % C::NP0;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
   __syncthreads();
 
   constexpr int NA = C::NA;
-  constexpr int CPP = (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) ? (C::RY + 1) + NA : NA;
+  constexpr int CPP = MODE == Mode::SpF16x2 ? (C::RY + 1) + NA : NA;
   constexpr int NZ = 2 * C::RZ + 1;
   constexpr int NWT = (2 * C::RY + 1) * (2 * C::RX + 1);
   // operands: all dz planes (small stencils) or one plane at a time
@@ -81,17 +81,10 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
         Ad[k][a][0] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 0];
         Ad[k][a][1] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 1];
       }
-    } else if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) {
-#pragma unroll
-      for (int c = 0; c <= C::RY; ++c) {
-        Am[k][c] = args.a_words[(size_t)(dzi * CPP + c) * 32 + lane];
-        Em[k][c] = args.meta[(size_t)(dzi * CPP + c) * 32 + lane];
-      }
-#pragma unroll
-      for (int a = 0; a < NA; ++a) {
-        A[k][a] = args.a_words[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
-        E[k][a] = args.meta[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
-      }
+    } else if (MODE == Mode::SpF16x2) {
+      load_split_operands<C>(args, dzi * CPP, lane, Am[k], Em[k], A[k], E[k]);
+    } else if (MODE == Mode::SpBF16x3) {
+      // two passes of operands, loaded by plane_split
     } else {
 #pragma unroll
       for (int i = 0; i < NWT; ++i) W[i] = args.w[(size_t)dzi * NWT + i];
@@ -130,12 +123,12 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
       if (z == z0) {
         for (int zi = z0 - C::RZ; zi <= z0 + C::RZ; ++zi) {
           const int s = slot_of(zi);
-          ok = ok && mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status);
+          ok = ok && mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status, args.wait_cycles);
           phases ^= 1u << s;
           pending &= ~(1u << s);
         }
       } else {
-        ok = ok && mbar_wait_bounded(&bar[sn], (phases >> sn) & 1, args.status);
+        ok = ok && mbar_wait_bounded(&bar[sn], (phases >> sn) & 1, args.status, args.wait_cycles);
         phases ^= 1u << sn;
         pending &= ~(1u << sn);
       }
@@ -208,15 +201,11 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           } else if (MODE == Mode::DenseTF32) {
             if (centre_only) plane_dense_tf32_centre<C, C::SX, RIN>(row0, Ad[k], acc);
             else plane_dense_tf32<C, C::SX, RIN>(row0, Ad[k], acc);
-          } else if (MODE == Mode::SpF16x2) plane_sp_split<C, false>(row0, Am[k], Em[k], A[k], E[k], acc, accC);
-          else plane_sp_split<C, true>(row0, Am[k], Em[k], A[k], E[k], acc, acc);
+          } else {
+            plane_split<C, MODE>(args, dzi, lane, row0, Am[k], Em[k], A[k], E[k], acc, accC);
+          }
         }
-        if (MODE == Mode::SpF16x2) {
-#pragma unroll
-          for (int i = 0; i < C::H / 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(accC[i][j], 1.0f / 2048.0f, acc[i][j]);
-        }
+        if (MODE == Mode::SpF16x2 || MODE == Mode::SpBF16x3) combine_split<MODE>(acc, accC);
         if (is_tf32_mode(MODE) && args.out_tf32) round_tf32_inplace(acc);
         float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.pitch + xbase + 16 * q + g;
         const int pitch = (int)args.pitch;
@@ -254,7 +243,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
       // loads still in flight after a wait ran out: wait for them (bounded)
       if (tid == 0)
         for (int s = 0; s < C::NP; ++s)
-          if ((pending >> s) & 1) (void)mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status);
+          if ((pending >> s) & 1) (void)mbar_wait_bounded(&bar[s], (phases >> s) & 1, args.status, args.wait_cycles);
       break;
     }
     rot = (rot + (z1 - z0) + 2 * C::RZ) % C::NP;

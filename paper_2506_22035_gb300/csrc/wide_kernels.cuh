@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
     float* S = stage(s);
     const int x0 = (t % args.tiles_x) * C::BX, y0 = (t / args.tiles_x) * C::BY;
     if (use_tma) {
-      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status, args.wait_cycles);
       if (!__syncthreads_and(ok)) break;
     } else {
       load_box_async(args.src, args.nx, args.ny, 1, (int64_t)x0 - kWideHalo, (int64_t)y0 - C::RY, 0, C::SX, C::SY,
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
   if (use_tma && tid == 0) {
     for (int k = 0; k < 2; ++k) {
       const int t = blockIdx.x + (it + k) * gridDim.x;
-      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status, args.wait_cycles);
     }
   }
 }
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(C::kThreads)
     float* S = stage(s);
     const int64_t x0 = (int64_t)t * C::NT;
     if (use_tma) {
-      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+      const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status, args.wait_cycles);
       if (!__syncthreads_and(ok)) break;
     } else {
       load_box_async(args.src, n, 1, 1, x0 - kWideHalo, 0, 0, C::kChunk, 1, 1, S, wy, C::kThreads / 32, lane);
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(C::kThreads)
   if (use_tma && tid == 0) {
     for (int k = 0; k < 2; ++k) {
       const int t = blockIdx.x + (it + k) * gridDim.x;
-      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status, args.wait_cycles);
     }
   }
 }
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(C::kThreads)
     const int s = it & 1;
     float* S = in_stage(s);
     const int64_t x0 = (int64_t)t * C::NT;
-    const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status);
+    const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1, args.status, args.wait_cycles);
     if (!__syncthreads_and(ok)) break;
     if (RIN) {
       for (int i = tid; i < C::kBuf; i += C::kThreads) S[i] = __uint_as_float(cvt_tf32(S[i]));
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(C::kThreads)
   if (tid == 0) {
     for (int k = 0; k < 2; ++k) {
       const int t = blockIdx.x + (it + k) * gridDim.x;
-      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status);
+      if (t < ntiles) (void)mbar_wait_bounded(&full[(it + k) & 1], ((it + k) >> 1) & 1, args.status, args.wait_cycles);
     }
   }
 }

@@ -171,6 +171,19 @@ def serving_arrivals(n: int = 2000, rate_per_s: float = 200.0, workload: int = 4
     return jobs
 
 
+def serving_grid_pool(jobs, workload: int = 4) -> np.ndarray:
+    """One U[0,1) float32 buffer as large as the largest job of `jobs`; each
+    serving job's grid is its prefix, reshaped (drawing every job's grid of up
+    to 512^3 points on the host would take longer than serving it)."""
+    n = max(int(np.prod(j.extents)) for j in jobs)
+    return grid((n,), 0.0, 1.0, rng(workload, 7))
+
+
+def serving_job_coeffs(job: Job) -> np.ndarray:
+    """The serving job's coefficients: normalised random from its own seed."""
+    return normalised_coeffs(job.ndim, job.r, job.shape, np.random.Generator(np.random.PCG64(job.seed + 1)))
+
+
 def job_inputs(job: Job):
     g = np.random.Generator(np.random.PCG64(job.seed))
     u0 = grid(job.extents, 0.0, 1.0, g)

@@ -84,7 +84,8 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     assert lib.spider_plan_set_steps_per_pass(p.handle, 11) == _native.SPIDER_ERR_UNSUPPORTED
     assert lib.spider_plan_set_steps_per_pass(p.handle, 10) == _native.SPIDER_OK   # radius 1: deep tiles
     assert lib.spider_plan_set_steps_per_pass(p.handle, 3) == _native.SPIDER_OK
-    assert lib.spider_plan_set_tile_variant(p.handle, 5) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_plan_set_tile_variant(p.handle, 6) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_plan_set_tile_variant(p.handle, 5) == _native.SPIDER_OK
     assert lib.spider_plan_set_tile_variant(p.handle, 4) == _native.SPIDER_OK
     assert lib.spider_plan_set_tile_variant(p.handle, 1) == _native.SPIDER_OK
     assert lib.spider_plan_autotune(p.handle, None, None, 1, None, None, None) == _native.SPIDER_ERR_INVALID
@@ -92,6 +93,46 @@ def test_run_rejects_bad_arguments_without_touching_a_device(lib):
     p3 = spider.Plan(np.ones((5, 5, 5), np.float32), (8, 8, 8))  # 3-D fusion is built for r = 1 only
     assert lib.spider_plan_set_steps_per_pass(p3.handle, 2) == _native.SPIDER_ERR_UNSUPPORTED
     p3.close()
+
+
+def test_failure_hooks_validate_their_arguments(lib):
+    assert lib.spider_set_wait_limit(999) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch_drop_item(-2) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_batch_drop_item(-1) == 0
+
+
+def test_error_bound_model(lib):
+    # bound = steps * (weight-sum error + drift) + floor, per arithmetic;
+    # radius 4..7 has no split or comparator kernel
+    w = si_coeffs(2, 2)
+    p = spider.Plan(w, (64, 64), "box", "tf32")
+    b = {k: [p.error_bound(n, *k) for n in (0, 100, 200)] for k in
+         (("tf32", "sparse_tc"), ("f16x2", "sparse_tc"), ("bf16x3", "sparse_tc"), ("tf32", "cuda_core"))}
+    for v in b.values():
+        assert 0 < v[0] < v[1] < v[2]
+        assert abs((v[2] - v[1]) - (v[1] - v[0])) <= 1e-12 * v[2]     # linear in the step count
+    assert b[("tf32", "cuda_core")][2] < b[("f16x2", "sparse_tc")][2] < b[("tf32", "sparse_tc")][2]
+    with pytest.raises(spider.SpiderError):
+        p.error_bound(-1)
+    p.close()
+    wide = spider.Plan(si_coeffs(2, 6), (64, 64), "box", "tf32")
+    assert wide.error_bound(10) > 0
+    for k in (("f16x2", "sparse_tc"), ("tf32", "cuda_core"), ("tf32", "dense_tc")):
+        with pytest.raises(spider.SpiderError) as ei:
+            wide.error_bound(10, *k)
+        assert ei.value.status == 2
+    wide.close()
+
+
+def si_coeffs(ndim, r):
+    import stencil_inputs as si
+    return si.normalised_coeffs(ndim, r, "box", si.rng(80, r))
+
+
+def test_plan_owns_no_device_memory_before_its_first_run(lib):
+    p = spider.Plan(si_coeffs(2, 1), (64, 64), "box", "tf32")
+    assert p.device_bytes() == 0
+    p.close()
 
 
 def test_batch_rejects_bad_arguments_without_touching_a_device(lib):
@@ -251,7 +292,8 @@ def test_split_operands_have_expected_layout(prec):
     w /= w.sum()
     p = spider.Plan(w, (16, 16), "box", prec)
     words, meta = p.operands()
-    combos = (3 + 1) + 8                    # (ry+1) hi*hi combos + (2ry+2) correction combos
+    passes = 2 if prec == "bf16x3" else 1
+    combos = passes * ((3 + 1) + 8)         # per pass: (ry+1) two-row combos + (2ry+2) one-row combos
     assert words.size == combos * 128 and meta.size == combos * 32
     # metadata nibbles: two increasing 2-bit indices per group, lanes q >= 2 unused
     m = meta.reshape(combos, 32)
@@ -263,6 +305,134 @@ def test_split_operands_have_expected_layout(prec):
             for k in range(8):
                 nib = (int(m[c, lane]) >> (4 * k)) & 0xF
                 assert (nib & 3) < (nib >> 2)
+    p.close()
+
+
+def b_fragment_rows():
+    """Sec. 3.2's row-offset equation for a 16-bit B fragment (golden fixture):
+    rows[q][i] = K row of element i held by lanes with lane mod 4 = q."""
+    path = os.path.join(ROOT, "tests", "golden", "b_fragment_rows_m16n8k16.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = [int(x) for x in line.split()]
+            rows[f[0]] = f[1:]
+    return rows
+
+
+def bits16_to_f32(u, bf16):
+    u = np.asarray(u, np.uint16)
+    if bf16:
+        return (u.astype(np.uint32) << 16).view(np.float32)
+    return u.view(np.float16).astype(np.float32)
+
+
+def rn16(x, bf16):
+    """Round float32 to FP16 / BF16 (nearest, ties to even), as float32."""
+    x = np.asarray(x, np.float32)
+    if not bf16:
+        return x.astype(np.float16).astype(np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def decode_16bit_k32(words, meta, bf16):
+    """One packed m16n8k32 A operand -> the two 16 x 16 window matrices it
+    multiplies (K half 0, K half 1).  Values and metadata decode to a 16 x 32
+    matrix in MMA K order (group c of 4 K indices, nibble = idx0 | idx1 << 2);
+    K row -> window position follows the kernel's loads: lane q loads window
+    positions 4 sigma(q) + i (i = 0..3) and hands element i to the K row the
+    paper's B-fragment equation gives (plus 16 for the second half)."""
+    comp = np.zeros((16, 16), np.float32)
+    for lane in range(32):
+        g, q = divmod(lane, 4)
+        wv = words[lane]
+        for reg, (row, col) in enumerate(((g, 2 * q), (g + 8, 2 * q), (g, 2 * q + 8), (g + 8, 2 * q + 8))):
+            comp[row, col] = bits16_to_f32(int(wv[reg]) & 0xFFFF, bf16)
+            comp[row, col + 1] = bits16_to_f32(int(wv[reg]) >> 16, bf16)
+    K = np.zeros((16, 32), np.float32)
+    for lane in range(32):
+        g, q = divmod(lane, 4)
+        if q >= 2:
+            continue
+        for i in range(4):
+            grp = 4 * q + i
+            for half, row in ((0, g), (16, g + 8)):
+                nib = (int(meta[lane]) >> (half + 4 * i)) & 0xF
+                idx = (nib & 3, nib >> 2)
+                for s in range(2):
+                    K[row, 4 * grp + idx[s]] += comp[row, 2 * grp + s]
+    rows = b_fragment_rows()
+    H = np.zeros((2, 16, 16), np.float32)
+    for h in range(2):
+        for q in range(4):
+            for i in range(4):
+                H[h][:, 4 * SIGMA[q] + i] = K[:, 16 * h + rows[q][i]]
+    return H
+
+
+@pytest.mark.parametrize("prec", ["f16x2", "bf16x3"])
+@pytest.mark.parametrize("ndim,r", [(2, 1), (2, 3), (3, 1)])
+def test_split_operands_decode_to_sum_preserving_split_weights(prec, ndim, r):
+    bf16 = prec == "bf16x3"
+    gen = np.random.default_rng(200 + 10 * ndim + r)
+    w = gen.uniform(0, 1, (2 * r + 1,) * ndim)
+    w = (w / w.sum()).astype(np.float32)
+    p = spider.Plan(w, (8,) * ndim, "box", prec)
+    words, meta = p.operands()
+    ry = r if ndim >= 2 else 0
+    rz = r if ndim == 3 else 0
+    na = 2 * ry + 2
+    per_pass = (ry + 1) + na
+    passes = 2 if bf16 else 1
+    cpp = passes * per_pass
+    planes = 2 * rz + 1
+    assert words.size == planes * cpp * 128 and meta.size == planes * cpp * 32
+    words = words.reshape(-1, 32, 4)
+    meta = meta.reshape(-1, 32)
+    w3 = w.reshape((planes, 2 * ry + 1, 2 * r + 1))
+    dec = lambda c: decode_16bit_k32(words[c], meta[c], bf16)  # noqa: E731
+    # split terms read back from the top row of the one-row combos
+    # [K_hi(a) | K_y(a)] of each pass (a = 0 .. 2ry): y = lo (FP16), mid then lo (BF16)
+    hi = np.zeros_like(w3)
+    ys = [np.zeros_like(w3) for _ in range(passes)]
+    for dzi in range(planes):
+        for pz in range(passes):
+            for a in range(2 * ry + 1):
+                Hh = dec(dzi * cpp + pz * per_pass + (ry + 1) + a)
+                hi[dzi, a] = Hh[0][0, 4 - r:5 + r]
+                ys[pz][dzi, a] = Hh[1][0, 4 - r:5 + r]
+    two_row_terms = [hi] + ([ys[0]] if bf16 else [])  # pass 0: hi, BF16 pass 1: mid
+    for dzi in range(planes):
+        for pz in range(passes):
+            for c in range(ry + 1):
+                Hh = dec(dzi * cpp + pz * per_pass + c)
+                for h in range(2):
+                    exp = expected_window(two_row_terms[pz], 2 * c + h, ry, r, dzi).astype(np.float32)
+                    assert np.array_equal(Hh[h], exp), (dzi, pz, c, h)
+            for a in range(na):
+                Hh = dec(dzi * cpp + pz * per_pass + (ry + 1) + a)
+                assert np.array_equal(Hh[0], expected_window(hi, a, ry, r, dzi).astype(np.float32))
+                assert np.array_equal(Hh[1], expected_window(ys[pz], a, ry, r, dzi).astype(np.float32))
+    # hi (and BF16 mid) round to nearest; the last term is one of the two
+    # 16-bit neighbours of what is left, chosen so the split weights sum at
+    # least as close to the FP32 sum as rounding every term to nearest
+    assert np.array_equal(hi, rn16(w3, bf16))
+    if bf16:
+        mid, lo, scale = ys[0], ys[1], 1.0
+        assert np.array_equal(mid, rn16(w3 - hi, bf16))
+        rest = w3 - hi - mid
+    else:
+        mid, lo, scale = np.zeros_like(hi), ys[0], 1.0 / 2048
+        rest = (w3 - hi) * np.float32(2048)
+    rn = rn16(rest, bf16)
+    ulp_rn = np.abs(rn16(rn * np.float32(1 + 2 ** -6), bf16) - rn)   # spacing near each residual
+    assert np.all(np.abs(lo.astype(np.float64) - rest) <= np.maximum(ulp_rn, 2.0 ** -133) * 1.0001)
+    true_sum = w3.astype(np.float64).sum()
+    split = lambda last: (hi.astype(np.float64) + mid + scale * last.astype(np.float64)).sum()  # noqa: E731
+    assert abs(split(lo) - true_sum) <= abs(split(rn) - true_sum)
+    assert abs(split(lo) - true_sum) <= scale * float(ulp_rn.max())
     p.close()
 
 
