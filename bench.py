@@ -768,24 +768,23 @@ def serving_run(spider, n_jobs=600, budget=120 * 10**9):
     t0 = time.perf_counter()
     base = jobs[0].arrival_s
 
-    def drain():
-        for t in list(pending):
-            done, _ = server.poll(t)
-            if done:
-                out = np.empty(pending.pop(t), np.float32)
-                _, l = server.poll(t, out)   # copies the result and releases the ticket
-                lat.append(l)
-                done_at.append(time.perf_counter() - t0)
+    def drain(timeout):
+        # collect finished jobs (spider_server_wait hands each out once)
+        t = server.wait(timeout)
+        while t is not None:
+            out = np.empty(pending.pop(t), np.float32)
+            _, l = server.poll(t, out)   # copies the result and releases the ticket
+            lat.append(l)
+            done_at.append(time.perf_counter() - t0)
+            t = server.wait(0.0)
 
     for j, p in zip(jobs, plans):
         while time.perf_counter() - t0 < j.arrival_s - base:
-            drain()
-            time.sleep(0.0002)
+            drain(max(0.0, min(0.002, j.arrival_s - base - (time.perf_counter() - t0))))
         n = int(np.prod(j.extents))
         pending[server.submit(p, pool[:n].reshape(j.extents), j.steps, j.err_target)] = n
     while pending:
-        drain()
-        time.sleep(0.0005)
+        drain(0.05)
     server.close()
     for p in plans:
         p.close()

@@ -391,6 +391,12 @@ spider_status spider_submit(spider_server server, spider_plan plan, const float*
  * be read once).  latency_s (nullable) receives submit-to-completion seconds. */
 spider_status spider_poll(spider_server server, uint64_t ticket, float* out, int* done, double* latency_s);
 
+/* Waits up to timeout_s seconds for a job to finish and hands out its ticket
+ * (*got = 1), each finished job once, in order of completion; *got = 0 when
+ * none finished in time.  The job's record stays until spider_poll reads it,
+ * so a client waits here instead of polling every ticket. */
+spider_status spider_server_wait(spider_server server, double timeout_s, uint64_t* ticket, int* got);
+
 /* Stops the worker after the jobs already submitted finish, frees everything. */
 void spider_server_destroy(spider_server server);
 

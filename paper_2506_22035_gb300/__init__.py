@@ -246,6 +246,14 @@ class Server:
                                          ctypes.byref(lat)), "spider_poll")
         return bool(done.value), lat.value
 
+    def wait(self, timeout_s: float = 0.1):
+        """The ticket of a job that finished (each once, in completion order),
+        or None if none finished within timeout_s."""
+        t, got = ctypes.c_uint64(), ctypes.c_int()
+        check(_native.load().spider_server_wait(self._h, float(timeout_s), ctypes.byref(t), ctypes.byref(got)),
+              "spider_server_wait")
+        return t.value if got.value else None
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             _native.load().spider_server_destroy(self._h)

@@ -62,6 +62,7 @@ SIGNATURES = {
     "spider_server_create": (c_int, [c_size_t, ctypes.POINTER(c_void_p)]),
     "spider_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, ctypes.POINTER(c_uint64)]),
     "spider_poll": (c_int, [c_void_p, c_uint64, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
+    "spider_server_wait": (c_int, [c_void_p, c_double, ctypes.POINTER(c_uint64), ctypes.POINTER(c_int)]),
     "spider_server_destroy": (None, [c_void_p]),
     "spider_last_error": (ctypes.c_char_p, []),
 }

@@ -82,12 +82,10 @@ extern "C" spider_status spider_plan_autotune(spider_plan p, const float* grid_i
   for (int T = 1; T <= maxT && st == SPIDER_OK; ++T) {
     if (T > 4 && (!small2d || T > steps)) break;
     const int v0 = T > 4 ? 4 : 0;
-    // variant 5 (16-byte final-level stores) for 2-D sparse TF32 fused passes
-    const bool vec = p->ndim == 2 && T >= 2 && T <= 4 && p->engine == SPIDER_ENGINE_SPARSE_TC &&
-                     p->prec == SPIDER_TF32 && !p->wide();
-    const int nv = T == 1 ? 1 : vec ? 6 : small2d ? 5 : 4;
+    // variant 5 (16-byte final-level stores) measured slower than 2 and is
+    // not a candidate
+    const int nv = T == 1 ? 1 : small2d ? 5 : 4;
     for (int v = v0; v < nv && st == SPIDER_OK; ++v) {
-      if (v == 4 && !small2d && T <= 4) continue;
       p->steps_per_pass = T;
       p->tile_variant = v;
       st = run_device(p, grid_in, grid_out, steps, stream);  // warm-up

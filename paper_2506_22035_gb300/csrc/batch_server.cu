@@ -1,21 +1,24 @@
 // Serving: continuous batching of stencil jobs on one GPU.
 //
 // spider_submit copies the job (plan parameters, host grid) into a FIFO queue.
-// A worker thread owns kSlots CUDA streams and a stream-ordered memory pool
-// (cudaMemPool_t) that keeps up to the HBM budget reserved.  Each loop it
-//  * admits queued jobs in arrival order while a stream slot is free and the
-//    job's device memory (three grids: current, next, and the plan's scratch)
-//    fits the HBM budget next to the jobs already on the device; a job's
-//    grids and its plan's buffers are allocated from the pool on the job's
-//    stream and returned to it there (cudaMallocFromPoolAsync /
-//    cudaFreeAsync), so admitting or finishing a job never waits for the
-//    device or for the other jobs' work;
-//  * advances every running job by one chunk of at most kChunkSteps time
-//    steps once its previous chunk has finished, so a job admitted while
-//    others run starts within one chunk and its kernels interleave with
-//    theirs on the device;
-//  * copies finished results back, frees their memory and records the
-//    submit-to-completion latency.
+// Three threads serve it, and none of them holds the server's lock while it
+// calls CUDA:
+//  * the worker owns kSlots CUDA streams and a stream-ordered memory pool
+//    (cudaMemPool_t) that keeps up to the HBM budget reserved.  It admits
+//    queued jobs in arrival order while a stream slot is free and the job's
+//    device memory (three grids: current, next, and the plan's scratch) fits
+//    the HBM budget next to the jobs already on the device; a job's grids
+//    and its plan's buffers are allocated from the pool on the job's stream
+//    and returned to it there (cudaMallocFromPoolAsync / cudaFreeAsync), so
+//    admitting or finishing a job never waits for the device or for the
+//    other jobs' work.  It advances every running job by one chunk of at most
+//    kChunkSteps time steps once its previous chunk has finished, so a job
+//    admitted while others run starts within one chunk and its kernels
+//    interleave with theirs on the device;
+//  * an upload thread copies admitted jobs' grids to the device, and a
+//    download thread copies finished results back and records the
+//    submit-to-completion latency.  Host copies (of pageable memory) thus
+//    never stall the launches of the other jobs.
 // A job's arithmetic does not depend on what else runs: the result is the
 // same as a lone spider_run of the same plan in the arithmetic chosen for
 // it.  The arithmetic is the fastest whose a priori error bound
@@ -39,7 +42,7 @@
 namespace spider {
 namespace {
 
-constexpr int kSlots = 8;
+constexpr int kSlots = 16;
 constexpr int64_t kChunkSteps = 16;
 constexpr size_t kMaxQueued = 1 << 16;
 
@@ -50,13 +53,14 @@ struct Job {
   spider_plan plan = nullptr;
   double bound = 0;         // a priori error bound of the chosen arithmetic
   int64_t steps = 0, done_steps = 0;
-  std::vector<float> host;  // input at submit, result when done
+  std::unique_ptr<float[]> host;  // input at submit, result when done
+  size_t npts = 0;
   float* cur = nullptr;
   float* nxt = nullptr;
   size_t reserve = 0;       // bytes charged against the budget
   int slot = -1;
   cudaEvent_t ev = nullptr;
-  bool copying = false, finished = false;
+  bool finished = false;
   spider_status status = SPIDER_OK;
   std::string error;
   Clock::time_point t_submit, t_done;
@@ -69,16 +73,23 @@ struct spider_server_t {
   size_t budget = 0, used = 0;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv;
-  std::deque<spider::Job*> pending;
-  std::vector<spider::Job*> running;
+  std::condition_variable cv;       // wakes the worker
+  std::condition_variable copy_cv;  // wakes the copy threads
+  std::condition_variable done_cv;  // wakes spider_server_wait
+  std::deque<uint64_t> completed;   // finished tickets not yet handed out by spider_server_wait
+  std::deque<spider::Job*> pending;    // submitted, waiting for admission
+  std::deque<spider::Job*> uploads;    // admitted, grid to copy to the device
+  std::deque<spider::Job*> ready;      // on the device, first chunk to launch
+  std::deque<spider::Job*> downloads;  // computed (or failed), result to copy back
+  int uploading = 0;                   // uploads taken by the upload thread, not yet ready
   std::map<uint64_t, std::unique_ptr<spider::Job>> jobs;
   uint64_t next_ticket = 1;
-  bool stop = false;
+  bool stop = false;       // no more submissions: finish what is queued
+  bool worker_done = false;
   cudaStream_t streams[spider::kSlots] = {};
   bool slot_busy[spider::kSlots] = {};
   cudaMemPool_t pool = nullptr;
-  std::thread worker;
+  std::thread worker, uploader, downloader;
 };
 
 namespace spider {
@@ -92,8 +103,55 @@ size_t job_bytes(const spider_plan_t* p) {
   return b;
 }
 
-void finish(spider_server_t* s, Job* j, spider_status st, const std::string& err) {
-  // stream-ordered frees: after the job's own work, without waiting for it
+// Copies n floats, a few threads for large grids (one host thread copies at
+// about 12 GB/s on the GPU machine's host, a fraction of its memory bandwidth).
+void parallel_copy(float* dst, const float* src, int64_t n) {
+  const int64_t kPerThread = int64_t(1) << 22;
+  const int nt = (int)std::min<int64_t>(8, std::max<int64_t>(1, n / kPerThread));
+  const int64_t chunk = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) {
+    const int64_t a = std::min(n, t * chunk), b = std::min(n, (t + 1) * chunk);
+    th.emplace_back([=] { std::memcpy(dst + a, src + a, (size_t)(b - a) * sizeof(float)); });
+  }
+  std::memcpy(dst, src, (size_t)std::min(n, chunk) * sizeof(float));
+  for (auto& x : th) x.join();
+}
+
+// Copies n floats and returns the largest |value| (NaN counts as larger than
+// every finite value), in one pass: a few threads for large grids.  The
+// largest |value| decides whether the FP16 split can hold the field.
+float copy_and_max_abs(float* dst, const float* src, int64_t n) {
+  auto part = [](float* d, const float* s, int64_t m) {
+    uint32_t mx = 0;  // |x| as bits: integer order = magnitude order for non-negative floats
+    for (int64_t i = 0; i < m; ++i) {
+      uint32_t b;
+      std::memcpy(&b, s + i, 4);
+      d[i] = s[i];
+      mx = std::max(mx, b & 0x7FFFFFFFu);
+    }
+    return mx;
+  };
+  const int64_t kPerThread = int64_t(1) << 22;
+  const int nt = (int)std::min<int64_t>(8, std::max<int64_t>(1, n / kPerThread));
+  std::vector<uint32_t> mx(nt, 0);
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (int t = 1; t < nt; ++t) {
+    const int64_t a = std::min(n, t * chunk), b = std::min(n, (t + 1) * chunk);
+    th.emplace_back([&, t, a, b] { mx[t] = part(dst + a, src + a, b - a); });
+  }
+  mx[0] = part(dst, src, std::min(n, chunk));
+  for (auto& x : th) x.join();
+  const uint32_t m = *std::max_element(mx.begin(), mx.end());
+  float f;
+  std::memcpy(&f, &m, 4);
+  return f;
+}
+
+// Device side of finishing a job (no lock held): stream-ordered frees after
+// the job's own work, without waiting for it.
+void release_device(spider_server_t* s, Job* j) {
   cudaStream_t js = j->slot >= 0 ? s->streams[j->slot] : nullptr;
   if (j->cur) cudaFreeAsync(j->cur, js);
   if (j->nxt) cudaFreeAsync(j->nxt, js);
@@ -102,6 +160,10 @@ void finish(spider_server_t* s, Job* j, spider_status st, const std::string& err
   j->ev = nullptr;
   if (j->plan) spider_plan_destroy(j->plan);
   j->plan = nullptr;
+}
+
+// Bookkeeping of finishing a job (lock held): its slot and budget return.
+void mark_done(spider_server_t* s, Job* j, spider_status st, const std::string& err) {
   if (j->slot >= 0) s->slot_busy[j->slot] = false;
   j->slot = -1;
   s->used -= j->reserve;
@@ -110,86 +172,165 @@ void finish(spider_server_t* s, Job* j, spider_status st, const std::string& err
   j->error = err;
   j->finished = true;
   j->t_done = Clock::now();
+  s->completed.push_back(j->ticket);
+  s->cv.notify_all();
+  s->done_cv.notify_all();
 }
 
-// Enqueues the job's next chunk (or the copy-back) on its stream.
-void advance(spider_server_t* s, Job* j) {
+// Enqueues the job's next chunk on its stream (worker thread, no lock held).
+spider_status advance(spider_server_t* s, Job* j) {
   cudaStream_t st = s->streams[j->slot];
-  if (j->done_steps < j->steps) {
-    const int64_t n = std::min<int64_t>(kChunkSteps, j->steps - j->done_steps);
+  const int64_t n = std::min<int64_t>(kChunkSteps, j->steps - j->done_steps);
+  if (n > 0) {
     spider_status r;
     {
       std::lock_guard<std::mutex> lock(j->plan->mu);
       r = run_device(j->plan, j->cur, j->nxt, n, st);
     }
-    if (r != SPIDER_OK) { finish(s, j, r, spider_last_error()); return; }
+    if (r != SPIDER_OK) return r;
     std::swap(j->cur, j->nxt);
     j->done_steps += n;
-  } else {
-    cudaError_t e = cudaMemcpyAsync(j->host.data(), j->cur, j->host.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) { finish(s, j, SPIDER_ERR_CUDA, cudaGetErrorString(e)); return; }
-    j->copying = true;
   }
-  cudaEventRecord(j->ev, st);
-}
-
-bool admit(spider_server_t* s, Job* j) {
-  int slot = -1;
-  for (int k = 0; k < kSlots; ++k)
-    if (!s->slot_busy[k]) { slot = k; break; }
-  if (slot < 0 || s->used + j->reserve > s->budget) return false;
-  const size_t bytes = j->host.size() * sizeof(float);
-  cudaStream_t st = s->streams[slot];
-  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->cur), bytes, s->pool, st);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->nxt), bytes, s->pool, st);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    if (j->cur) cudaFreeAsync(j->cur, st);
-    if (j->nxt) cudaFreeAsync(j->nxt, st);
-    j->cur = j->nxt = nullptr;
-    return false;  // device memory is short right now: retry when a job finishes
-  }
-  s->slot_busy[slot] = true;
-  j->slot = slot;
-  s->used += j->reserve;
-  // the plan's own buffers come from the pool too, on the job's stream
-  j->plan->dev.pool = s->pool;
-  j->plan->dev.pool_stream = st;
-  e = cudaMemcpyAsync(j->cur, j->host.data(), bytes, cudaMemcpyHostToDevice, s->streams[slot]);
-  if (e != cudaSuccess) { finish(s, j, SPIDER_ERR_CUDA, cudaGetErrorString(e)); return true; }
-  s->running.push_back(j);
-  advance(s, j);
-  return true;
+  const cudaError_t e = cudaEventRecord(j->ev, st);
+  return e == cudaSuccess ? SPIDER_OK : SPIDER_ERR_CUDA;
 }
 
 void worker_loop(spider_server_t* s) {
   cudaSetDevice(s->device);
+  std::vector<Job*> running;  // worker-owned: chunks in flight
   std::unique_lock<std::mutex> lock(s->mu);
   for (;;) {
-    // admission in arrival order
-    while (!s->pending.empty() && admit(s, s->pending.front())) s->pending.pop_front();
-    // progress
-    bool progressed = false;
-    for (size_t i = 0; i < s->running.size();) {
-      Job* j = s->running[i];
-      if (!j->finished && cudaEventQuery(j->ev) == cudaSuccess) {
-        progressed = true;
-        if (j->copying) finish(s, j, SPIDER_OK, "");
-        else advance(s, j);
+    // admission in arrival order: reserve a slot and the job's memory
+    std::vector<Job*> admitted;
+    while (!s->pending.empty()) {
+      Job* j = s->pending.front();
+      int slot = -1;
+      for (int k = 0; k < kSlots; ++k)
+        if (!s->slot_busy[k]) { slot = k; break; }
+      if (slot < 0 || s->used + j->reserve > s->budget) break;
+      s->slot_busy[slot] = true;
+      j->slot = slot;
+      s->used += j->reserve;
+      s->pending.pop_front();
+      admitted.push_back(j);
+    }
+    std::vector<Job*> starting(s->ready.begin(), s->ready.end());
+    s->ready.clear();
+    const bool quit = s->stop && s->pending.empty() && s->uploads.empty() && s->uploading == 0 &&
+                      starting.empty() && running.empty() && admitted.empty();
+    if (quit) break;
+    lock.unlock();
+
+    std::vector<std::pair<Job*, spider_status>> failed;
+    std::vector<Job*> to_upload, computed;
+    for (Job* j : admitted) {
+      cudaStream_t st = s->streams[j->slot];
+      const size_t bytes = j->npts * sizeof(float);
+      cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->cur), bytes, s->pool, st);
+      if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->nxt), bytes, s->pool, st);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        j->error = std::string("job grids: ") + cudaGetErrorString(e);
+        failed.push_back({j, SPIDER_ERR_OOM});
+        continue;
       }
-      if (j->finished) {
-        s->running.erase(s->running.begin() + i);
-        s->cv.notify_all();
+      // the plan's own buffers come from the pool too, on the job's stream
+      j->plan->dev.pool = s->pool;
+      j->plan->dev.pool_stream = st;
+      to_upload.push_back(j);
+    }
+    for (Job* j : starting) {
+      const spider_status r = advance(s, j);
+      if (r != SPIDER_OK) {
+        j->error = spider_last_error();
+        failed.push_back({j, r});
+      } else {
+        running.push_back(j);
+      }
+    }
+    bool progressed = !admitted.empty() || !starting.empty();
+    for (size_t i = 0; i < running.size();) {
+      Job* j = running[i];
+      if (cudaEventQuery(j->ev) != cudaSuccess) {
+        ++i;
+        continue;
+      }
+      progressed = true;
+      spider_status r = SPIDER_OK;
+      if (j->done_steps < j->steps) r = advance(s, j);
+      if (r != SPIDER_OK) {
+        j->error = spider_last_error();
+        failed.push_back({j, r});
+      } else if (j->done_steps >= j->steps) {
+        computed.push_back(j);
       } else {
         ++i;
+        continue;
       }
+      running.erase(running.begin() + i);
     }
-    if (s->stop && s->pending.empty() && s->running.empty()) break;
+    for (auto& f : failed) release_device(s, f.first);
+
+    lock.lock();
+    for (Job* j : to_upload) s->uploads.push_back(j);
+    for (Job* j : computed) s->downloads.push_back(j);
+    for (auto& f : failed) mark_done(s, f.first, f.second, f.first->error);
+    if (!to_upload.empty() || !computed.empty()) s->copy_cv.notify_all();
     if (!progressed) {
-      if (s->running.empty() && s->pending.empty()) s->cv.wait(lock);
+      if (running.empty()) s->cv.wait_for(lock, std::chrono::milliseconds(2));
       else s->cv.wait_for(lock, std::chrono::microseconds(50));
     }
+  }
+  s->worker_done = true;
+  s->copy_cv.notify_all();
+}
+
+// Host -> device copies of admitted jobs' grids.  The copy is stream-ordered
+// before the job's first chunk, which the worker launches once the job is
+// handed back as ready.
+void upload_loop(spider_server_t* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    s->copy_cv.wait(lock, [&] { return !s->uploads.empty() || s->worker_done; });
+    if (s->uploads.empty()) break;  // the worker has finished: nothing more comes
+    Job* j = s->uploads.front();
+    s->uploads.pop_front();
+    ++s->uploading;
+    lock.unlock();
+    const cudaError_t e = cudaMemcpyAsync(j->cur, j->host.get(), j->npts * sizeof(float), cudaMemcpyHostToDevice,
+                                          s->streams[j->slot]);
+    if (e != cudaSuccess) {
+      j->error = cudaGetErrorString(e);
+      release_device(s, j);
+    }
+    lock.lock();
+    --s->uploading;
+    if (e != cudaSuccess) mark_done(s, j, SPIDER_ERR_CUDA, j->error);
+    else s->ready.push_back(j);
+    s->cv.notify_all();
+  }
+}
+
+// Device -> host copies of computed results, then the job's memory returns
+// to the pool and its latency is recorded.
+void download_loop(spider_server_t* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    s->copy_cv.wait(lock, [&] { return !s->downloads.empty() || s->worker_done; });
+    if (s->downloads.empty()) break;
+    Job* j = s->downloads.front();
+    s->downloads.pop_front();
+    lock.unlock();
+    cudaStream_t st = s->streams[j->slot];
+    cudaError_t e = cudaMemcpyAsync(j->host.get(), j->cur, j->npts * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const std::string err = e == cudaSuccess ? "" : cudaGetErrorString(e);
+    release_device(s, j);
+    lock.lock();
+    mark_done(s, j, e == cudaSuccess ? SPIDER_OK : SPIDER_ERR_CUDA, err);
   }
 }
 
@@ -235,6 +376,8 @@ spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out) 
     return fail(SPIDER_ERR_CUDA, std::string("memory pool: ") + cudaGetErrorString(pe));
   }
   s->worker = std::thread(worker_loop, s);
+  s->uploader = std::thread(upload_loop, s);
+  s->downloader = std::thread(download_loop, s);
   *out = s;
   return SPIDER_OK;
 }
@@ -250,8 +393,9 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
   // the FP16 range: the input's largest magnitude, the field not growing),
   // then FP32 on CUDA cores
   const int64_t npts = plan->points();
-  float amax = 0.f;
-  for (int64_t i = 0; i < npts; ++i) amax = std::max(amax, std::fabs(host_in[i]));
+  std::unique_ptr<float[]> host(new (std::nothrow) float[npts]);
+  if (!host) return fail(SPIDER_ERR_OOM, "host copy of the job's grid");
+  const float amax = copy_and_max_abs(host.get(), host_in, npts);
   struct Choice { spider_precision prec; spider_engine engine; };
   std::vector<Choice> choices = {{plan->prec, plan->engine}, {SPIDER_TF32, SPIDER_ENGINE_SPARSE_TC}};
   if (amax < 16384.f) choices.push_back({SPIDER_F16X2, SPIDER_ENGINE_SPARSE_TC});
@@ -288,7 +432,8 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
     spider_plan_destroy(copy);
     return fail(SPIDER_ERR_OOM, "job larger than the server's HBM budget");
   }
-  j->host.assign(host_in, host_in + copy->points());
+  j->host = std::move(host);
+  j->npts = (size_t)npts;
   j->t_submit = Clock::now();
   std::lock_guard<std::mutex> lock(s->mu);
   if (s->pending.size() >= kMaxQueued) {
@@ -306,20 +451,37 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
 spider_status spider_poll(spider_server s, uint64_t ticket, float* out, int* done, double* latency_s) {
   set_error("");
   if (!s || !done) return fail(SPIDER_ERR_INVALID, "bad arguments");
-  std::lock_guard<std::mutex> lock(s->mu);
-  auto it = s->jobs.find(ticket);
-  if (it == s->jobs.end()) return fail(SPIDER_ERR_INVALID, "unknown ticket");
-  Job* j = it->second.get();
-  *done = j->finished ? 1 : 0;
-  if (!j->finished) return SPIDER_OK;
-  if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
-  const spider_status st = j->status;
-  const std::string err = j->error;
-  if (out) {
-    if (st == SPIDER_OK) std::memcpy(out, j->host.data(), j->host.size() * sizeof(float));
-    s->jobs.erase(it);
+  std::unique_ptr<Job> owned;  // a released record, copied out without the lock
+  Job* j = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return fail(SPIDER_ERR_INVALID, "unknown ticket");
+    j = it->second.get();
+    *done = j->finished ? 1 : 0;
+    if (!j->finished) return SPIDER_OK;
+    if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+    if (out) {
+      owned = std::move(it->second);
+      s->jobs.erase(it);
+    }
+    if (j->status != SPIDER_OK) return fail(j->status, j->error);
   }
-  if (st != SPIDER_OK) return fail(st, err);
+  if (owned && out) parallel_copy(out, owned->host.get(), (int64_t)owned->npts);
+  return SPIDER_OK;
+}
+
+spider_status spider_server_wait(spider_server s, double timeout_s, uint64_t* ticket, int* got) {
+  set_error("");
+  if (!s || !ticket || !got || !(timeout_s >= 0)) return fail(SPIDER_ERR_INVALID, "bad arguments");
+  *got = 0;
+  std::unique_lock<std::mutex> lock(s->mu);
+  const auto until = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  s->done_cv.wait_until(lock, until, [&] { return !s->completed.empty(); });
+  if (s->completed.empty()) return SPIDER_OK;
+  *ticket = s->completed.front();
+  s->completed.pop_front();
+  *got = 1;
   return SPIDER_OK;
 }
 
@@ -330,7 +492,9 @@ void spider_server_destroy(spider_server s) {
     s->stop = true;
     s->cv.notify_all();
   }
-  if (s->worker.joinable()) s->worker.join();
+  if (s->worker.joinable()) s->worker.join();  // every job computed; the copy threads then drain
+  if (s->uploader.joinable()) s->uploader.join();
+  if (s->downloader.joinable()) s->downloader.join();
   for (int k = 0; k < kSlots; ++k) {
     cudaStreamSynchronize(s->streams[k]);  // the stream-ordered frees have run
     cudaStreamDestroy(s->streams[k]);

@@ -123,8 +123,9 @@ def box2d_reference():
     return u0, w, torch.from_numpy(ref).cuda()
 
 
-# measured full-grid errors (GB300) and the tolerances, about 3x measured
-BOX2D_FULL_TOL = {"tf32": 1e-3, "f16x2": 1e-5, "bf16x3": 1e-5}
+# full-grid errors measured on GB300 (TF32 3.0e-4, FP16 hi/lo 4.1e-6, BF16
+# hi/mid/lo 4.2e-7) and the tolerances, about three times measured
+BOX2D_FULL_TOL = {"tf32": 9e-4, "f16x2": 1.2e-5, "bf16x3": 1.3e-6}
 
 
 @pytest.mark.parametrize("prec", ["tf32", "f16x2", "bf16x3"])

@@ -22,13 +22,19 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 spider = pytest.importorskip("paper_2506_22035_gb300")
 
-# (relative L2, max point error / max |ref|)
+# (relative L2, max point error / max |ref|): about three times the largest
+# errors these tests measured on GB300 (relative L2 / point: sparse TF32
+# 6.4e-4 / 9.5e-4, dense TF32 4.6e-4 / 9.5e-4, FP16 hi/lo 5.0e-7 / 6.6e-7,
+# BF16 hi/mid/lo 8.1e-8 / 1.7e-7, CUDA-core FP32 1.2e-7 / 4.4e-7).  Tests on
+# small grids whose field decays fast over many fused steps (the deep radius-1
+# tiles, the 1-D fused passes) measured up to 2.5e-3 in TF32 and pass a
+# scale of 4.
 TOL = {
-    ("sparse_tc", "tf32"): (3e-3, 1e-2),
-    ("sparse_tc", "f16x2"): (2e-5, 1e-4),
-    ("sparse_tc", "bf16x3"): (2e-4, 1e-3),
-    ("dense_tc", "tf32"): (3e-3, 1e-2),
-    ("cuda_core", "tf32"): (2e-6, 2e-5),
+    ("sparse_tc", "tf32"): (2e-3, 3e-3),
+    ("sparse_tc", "f16x2"): (1.5e-6, 2e-6),
+    ("sparse_tc", "bf16x3"): (2.5e-7, 5e-7),
+    ("dense_tc", "tf32"): (1.5e-3, 3e-3),
+    ("cuda_core", "tf32"): (3.5e-7, 1.5e-6),
 }
 ALL = list(TOL)
 
@@ -49,8 +55,8 @@ def gpu_run(u0, w, steps, shape="box", prec="tf32", engine="sparse_tc", steps_pe
     return out
 
 
-def check_close(got, ref, key):
-    rel_tol, max_tol = TOL[key]
+def check_close(got, ref, key, scale=1.0):
+    rel_tol, max_tol = (scale * t for t in TOL[key])
     assert np.all(np.isfinite(got))
     ref_norm = np.linalg.norm(ref)
     rel = np.linalg.norm(got - ref) / ref_norm if ref_norm > 0 else np.linalg.norm(got)
@@ -460,7 +466,7 @@ def test_fused_1d_passes_match_single_steps(r, n):
     for T in (2, 3, 4):
         fused = gpu_run(u0, w, 9, "box", "tf32", "sparse_tc", T)
         assert np.array_equal(fused, single), (r, n, T)
-    check_close(single, oracle.stencil(u0, w, 9), ("sparse_tc", "tf32"))
+    check_close(single, oracle.stencil(u0, w, 9), ("sparse_tc", "tf32"), scale=4)
 
 
 @pytest.mark.parametrize("kind", ["star", "box"])
@@ -473,7 +479,7 @@ def test_deep_fusion_radius_1_matches_single_steps(kind, shape, steps):
     u0 = si.grid(shape, -1, 1, g)
     w = si.normalised_coeffs(2, 1, kind, g)
     single = gpu_run(u0, w, steps, kind, "tf32", "sparse_tc", 1)
-    check_close(single, oracle.stencil(u0, w, steps), ("sparse_tc", "tf32"))
+    check_close(single, oracle.stencil(u0, w, steps), ("sparse_tc", "tf32"), scale=4)
     for T in (5, 6, 7, 8, 9, 10):
         fused = gpu_run(u0, w, steps, kind, "tf32", "sparse_tc", T, 4)
         assert np.array_equal(fused, single), (shape, steps, T)
@@ -516,7 +522,7 @@ def test_autotune_keeps_results_within_tolerance():
     a = torch.from_numpy(u0).cuda()
     b = torch.empty_like(a)
     T, v = plan.autotune(a, b, 8)
-    assert 1 <= T <= 4 and v in (0, 1, 2, 3, 5)
+    assert 1 <= T <= 4 and v in (0, 1, 2, 3)
     plan.run(a, b, 8)
     plan.sync()
     ref = oracle.stencil(u0, w, 8)
@@ -675,18 +681,21 @@ def test_server_results_same_alone_and_in_the_mix():
     server = spider.Server(8 << 30)
     plans = [spider.Plan(w, u0.shape, kind, "tf32") for u0, w, kind, steps, err in jobs]
     tickets = [server.submit(p, u0, steps, err) for p, (u0, w, kind, steps, err) in zip(plans, jobs)]
+    shape_of = {t: u0.shape for t, (u0, *_rest) in zip(tickets, jobs)}
     results = {}
     t0 = time.time()
+    # spider_server_wait hands out each finished ticket once
     while len(results) < len(tickets) and time.time() - t0 < 120:
-        for t, (u0, *_rest) in zip(tickets, jobs):
-            if t in results:
-                continue
-            out = np.empty_like(u0)
-            done, lat = server.poll(t, out)
-            if done:
-                results[t] = (out, lat)
-        time.sleep(0.002)
+        t = server.wait(1.0)
+        if t is None:
+            continue
+        assert t in shape_of and t not in results
+        out = np.empty(shape_of[t], np.float32)
+        done, lat = server.poll(t, out)
+        assert done
+        results[t] = (out, lat)
     assert len(results) == len(tickets)
+    assert server.wait(0.0) is None
     picked = set()
     for t, p, (u0, w, kind, steps, err) in zip(tickets, plans, jobs):
         out, lat = results[t]
