@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--workload", default="box2d",
                     choices=sorted(WORKLOADS) + ["batched", "batched_small", "serving", "sweep", "mma_peak"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
-    ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core"])
+    ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core", "sparse_tc_copy"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
                     help="time steps fused per HBM pass (default: chosen by spider_plan_autotune)")
     ap.add_argument("--tile-variant", type=int, default=None)

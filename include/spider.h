@@ -266,10 +266,13 @@ void spider_plan_destroy(spider_plan plan);
 /* spider_batch -- advances n independent grids in one persistent launch.
  * plans[i], ins[i], outs[i], steps[i] as for spider_run (a plan may appear
  * once).  2-D grids with TF32 sparse plans go through one persistent kernel,
- * issued as a CUDA graph: work items (time step, grid, 64 x 128 tile) are
- * claimed from a device queue in step-major order, and step s of a tile
- * starts only after the tile and its eight neighbours finished step s-1
- * (per-tile counters, bounded waits).  Such grids of at least 2^16 points
+ * issued as a CUDA graph: work items (pass, grid, tile) are claimed from a
+ * device queue in pass-major order, and pass p of a tile starts only after
+ * the tile and its eight neighbours finished pass p-1 (per-tile counters,
+ * bounded waits).  A pass is two time steps on a (64 - 2r) x 120 tile (the
+ * first or last pass one step when the step count needs it), or one step on
+ * a 64 x 128 tile for one-step grids; see spider_batch_configure.  Results
+ * are bit-identical to spider_run's.  Such grids of at least 2^16 points
  * and more than one step run through spider_run with fused passes instead
  * (the plan's steps per pass and tile variant if it fuses, else the
  * autotuned choice of its kind of stencil, else 2 steps on variant 2), on
@@ -279,13 +282,24 @@ void spider_plan_destroy(spider_plan plan);
  * the persistent launch.  Grids whose rows are not a multiple of 4 floats,
  * or whose buffers are not 16-byte aligned, use the plan's padded grids (see
  * spider_run).  Synchronous: returns when all grids are done.  n <= 4096.
+ * Concurrent calls on one device (other threads or streams) run one after
+ * another: they share the library's side streams and work queue.
  * SPIDER_ERR_TIMEOUT if a dependency wait ran out. */
 spider_status spider_batch(int n, const spider_plan* plans, const float* const* ins, float* const* outs,
                            const int64_t* steps, cudaStream_t stream);
 
+/* spider_batch_configure -- routing of spider_batch.  Grids of at least
+ * fuse_min_points points (with more than one step) run as fused passes of
+ * their own on side streams; smaller grids run in the persistent queue, whose
+ * items take queue_steps_per_item time steps (1, or 2: the fused kernel's two
+ * levels on tiles of (64 - 2r) x 120 outputs).  0 restores a default (the
+ * measured best: 2^16 points, 2 steps per item).  Process-wide; applies to
+ * later calls. */
+spider_status spider_batch_configure(long long fuse_min_points, int queue_steps_per_item);
+
 /* ---- failure detection -------------------------------------------------------
  * The paper has no counterpart.  Every wait of the library's kernels (a TMA
- * load landing, a batch-queue item waiting for its neighbours' previous step)
+ * load landing, a batch-queue item waiting for its neighbours' previous pass)
  * is bounded: when it runs out, the kernel records a timeout in a device
  * status word and finishes without touching memory it does not own, the
  * CUDA context stays usable, and the call that reads the status word
@@ -299,8 +313,8 @@ spider_status spider_batch(int n, const spider_plan* plans, const float* const* 
  *
  * spider_batch_drop_item: a test hook.  The next spider_batch call leaves
  * item `item` of its persistent queue out (items numbered in the queue's
- * step-major order, from 0; -1 clears): the item is claimed but neither
- * loaded nor computed, and its tile's step counter is not advanced, so the
+ * pass-major order, from 0; -1 clears): the item is claimed but neither
+ * loaded nor computed, and its tile's pass counter is not advanced, so the
  * items that depend on it wait until the limit runs out and the call returns
  * SPIDER_ERR_TIMEOUT (that call's results are then undefined).  The hook
  * applies to one call and resets itself. */
@@ -376,10 +390,14 @@ spider_status spider_server_create(size_t hbm_budget_bytes, spider_server* out);
 /* Submits a job.  `plan` is copied (the caller may destroy it afterwards).
  * host_in: host grid of the plan's extents, copied before return.
  * err_target: relative L2 error the caller accepts.  The job runs in the
- * fastest arithmetic whose a priori bound (spider_plan_error_bound) for
- * `steps` steps of this stencil meets it, tried in this order: the plan's own
- * precision and engine, sparse TF32, the FP16 hi/lo split (only when every
- * |host_in| value is below 16384), FP32 on CUDA cores (radius <= 3).
+ * plan's own precision and engine if its a priori bound
+ * (spider_plan_error_bound) for `steps` steps meets the target, else in the
+ * arithmetic measured fastest for this class of stencil among those whose
+ * bound meets it: sparse TF32, the FP16 hi/lo split (only when every
+ * |host_in| value is below 16384), FP32 on CUDA cores (radius <= 3); with
+ * the plan's steps per pass if above 1, else the autotuner's choice for the
+ * kind of stencil if one was measured in the process, else a measured
+ * default of its class.
  * *ticket identifies the job.  SPIDER_ERR_UNSUPPORTED if no arithmetic built
  * for the stencil meets the target; SPIDER_ERR_OOM if the job alone exceeds
  * the budget; SPIDER_ERR_BUSY if the queue is full. */
@@ -390,6 +408,12 @@ spider_status spider_submit(spider_server server, spider_plan plan, const float*
  * copied to host memory `out` and the job's record is released (a ticket can
  * be read once).  latency_s (nullable) receives submit-to-completion seconds. */
 spider_status spider_poll(spider_server server, uint64_t ticket, float* out, int* done, double* latency_s);
+
+/* The arithmetic the server chose for a job (precision, engine, time steps
+ * per pass) and its a priori error bound; any pointer may be NULL.  Valid
+ * until spider_poll releases the ticket. */
+spider_status spider_server_job_arithmetic(spider_server server, uint64_t ticket, spider_precision* prec,
+                                          spider_engine* engine, int* steps_per_pass, double* bound);
 
 /* Waits up to timeout_s seconds for a job to finish and hands out its ticket
  * (*got = 1), each finished job once, in order of completion; *got = 0 when

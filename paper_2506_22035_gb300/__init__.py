@@ -171,6 +171,12 @@ def measure_mma_rate(kind: str = "sp_tf32", stream=None) -> float:
     return out.value
 
 
+def batch_configure(fuse_min_points: int = 0, queue_steps_per_item: int = 0) -> None:
+    """Routing of spider.batch (spider_batch_configure); 0 = default."""
+    check(_native.load().spider_batch_configure(int(fuse_min_points), int(queue_steps_per_item)),
+          "spider_batch_configure")
+
+
 def batch(plans, ins, outs, steps, stream=None) -> None:
     n = len(plans)
     P = (ctypes.c_void_p * n)(*[p.handle for p in plans])
@@ -246,6 +252,17 @@ class Server:
                                          ctypes.byref(lat)), "spider_poll")
         return bool(done.value), lat.value
 
+    def arithmetic(self, ticket: int):
+        """(precision, engine, steps_per_pass, a priori error bound) the server
+        chose for a job; valid until poll releases the ticket."""
+        p, e, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(_native.load().spider_server_job_arithmetic(self._h, ctypes.c_uint64(ticket), ctypes.byref(p),
+                                                          ctypes.byref(e), ctypes.byref(t), ctypes.byref(b)),
+              "spider_server_job_arithmetic")
+        prec = {v: k for k, v in PRECISIONS.items()}[p.value]
+        eng = {v: k for k, v in ENGINES.items()}[e.value]
+        return prec, eng, t.value, b.value
+
     def wait(self, timeout_s: float = 0.1):
         """The ticket of a job that finished (each once, in completion order),
         or None if none finished within timeout_s."""
@@ -267,5 +284,5 @@ class Server:
 
 
 __all__ = ["Plan", "Domain", "Server", "norms_fp64", "relative_l2_error", "constant_check_fp64", "batch", "SpiderError",
-           "measure_mma_rate",
+           "measure_mma_rate", "batch_configure",
            "PRECISIONS", "ENGINES", "SHAPES"]

@@ -47,6 +47,7 @@ SIGNATURES = {
     "spider_plan_destroy": (None, [c_void_p]),
     "spider_set_wait_limit": (c_int, [ctypes.c_longlong]),
     "spider_batch_drop_item": (c_int, [ctypes.c_longlong]),
+    "spider_batch_configure": (c_int, [ctypes.c_longlong, c_int]),
     "spider_batch": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                              ctypes.POINTER(c_int64), c_void_p]),
     "spider_domain_create": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_void_p)]),
@@ -62,6 +63,8 @@ SIGNATURES = {
     "spider_server_create": (c_int, [c_size_t, ctypes.POINTER(c_void_p)]),
     "spider_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, ctypes.POINTER(c_uint64)]),
     "spider_poll": (c_int, [c_void_p, c_uint64, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
+    "spider_server_job_arithmetic": (c_int, [c_void_p, c_uint64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                             ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "spider_server_wait": (c_int, [c_void_p, c_double, ctypes.POINTER(c_uint64), ctypes.POINTER(c_int)]),
     "spider_server_destroy": (None, [c_void_p]),
     "spider_last_error": (ctypes.c_char_p, []),

@@ -3,28 +3,34 @@
 // a device work queue; larger grids run as fused multi-step passes of their
 // own on side streams beside it (see kFuseMinPoints).
 //
-// Queue work items are (time step s, job, tile) in step-major order; CTAs
-// claim them with one atomic counter.  Item (s, j, tile) reads job j's grid
-// of step s over the tile plus its halo, so it may start only after the tile
-// and its eight neighbours have finished step s-1 (those are also the last
-// readers of the buffer it overwrites).  Each job keeps one completion counter
-// per tile; a producer warp waits on the neighbours' counters with bounded
-// spins (acquire loads) and publishes a tile's counter with a release store
-// once every consumer warp has handed the tile's stage back.  Because every
-// CTA claims and processes its items in global order and an item only waits
-// on items of an earlier step, every awaited item is already held by a
-// running CTA: the queue cannot deadlock, whatever the residency.
+// Queue work items are (pass p, job, tile) in pass-major order; CTAs claim
+// them with one atomic counter.  A pass is two time steps on the fused
+// kernel's level scheme (output tile (64 - 2r) x 120, level 1 of 64 x 128 in
+// shared memory, input box (64 + 2r) x 136), or one step: the first pass of
+// a job whose step count is odd or whose input rows TMA cannot describe, the
+// last when one step is left, and every pass of a one-step job (64 x 128
+// tile of stencil_step_kernel) or when spider_batch_configure asks for one
+// step per item.  Item (p, j, tile) reads job j's grid after pass p-1 over
+// the tile plus a halo narrower than a tile, so it may start only after the
+// tile and its eight neighbours have finished pass p-1 (those are also the
+// last readers of the buffer it overwrites).  Each job keeps one completion
+// counter per tile; a producer warp waits on the neighbours' counters with
+// bounded spins (acquire loads) and publishes a tile's counter with a
+// release store once every consumer warp has handed the tile's stage back.
+// Because every CTA claims and processes its items in global order and an
+// item only waits on items of an earlier pass, every awaited item is already
+// held by a running CTA: the queue cannot deadlock, whatever the residency.
 //
-// The tile computation is the one-step SPIDER tile of stencil_step_kernel
-// (TF32 sparse MMA, 64 x 128 outputs, TMA halo box).  Each job brings its own
-// tensor maps and packed operands.
+// Each job brings its own tensor maps and packed operands (TF32 sparse MMA).
 #include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include "fused_kernels.cuh"
 #include "launch.h"
 #include "stencil_kernels.cuh"
 
@@ -40,8 +46,10 @@ constexpr int kBY = 64, kBX = 128, kWarpsY = 4, kWarpsX = 2, kH = 16;
 constexpr int kThreads = kWarpsY * kWarpsX * 32;
 constexpr int kMaxStageFloats = (kBY + 2 * kMaxR) * (kBX + 2 * kHaloX);
 constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
-constexpr int kSmemBase = 2 * kStageStride + 1024 + 128;  // stages, alignment, barriers, slots
-constexpr int kMaxTableSmem = 48 * 1024;
+// stages, alignment, barriers and slots, the level buffer of two-step items
+constexpr int kSmemBase = 2 * kStageStride + 1024 + 128 + 64 * 128 * 4;
+// queue tables go to shared memory only while two CTAs still fit on an SM
+constexpr int kMaxTableSmem = 4 * 1024;
 // Grids of at least this many points (with more than one step) run as fused
 // passes of their own on side streams; smaller ones, and single steps, go
 // through the persistent queue.  Measured on the mixed batch of 64 grids of
@@ -53,13 +61,22 @@ constexpr int kMaxTableSmem = 48 * 1024;
 // Below it the queue wins: 256 grids of 32^2..255^2 points run at 188
 // GStencil/s through it and at 41 as fused passes on side streams.
 constexpr long long kFuseMinPoints = 1LL << 16;
+constexpr int kQueueStepsPerItem = 2;
+// Routing of spider_batch (spider_batch_configure): grids of at least
+// g_fuse_min_points points (and more than one step) run as fused passes on
+// side streams; queue items take g_queue_steps steps (1 or 2).
+std::atomic<long long> g_fuse_min_points{kFuseMinPoints};
+std::atomic<int> g_queue_steps{kQueueStepsPerItem};
 
 // Queue item the next spider_batch call leaves out (spider_batch_drop_item), -1: none.
 std::atomic<long long> g_drop_item{-1};
 constexpr int kSideStreams = 8;                  // streams the fused grids run on, next to the queue
 
 // Non-blocking streams for the grids that run as fused passes beside the
-// persistent queue, kept per device for the process.
+// persistent queue, kept per device for the process.  spider_batch calls on
+// one device take batch_lock(dev) for their whole duration, so two calls
+// (from different threads or caller streams) never share these streams at
+// the same time: one call's join never waits on another call's work.
 cudaStream_t side_stream(int dev, int k) {
   static std::mutex mu;
   static cudaStream_t pool[64][kSideStreams] = {};
@@ -70,6 +87,11 @@ cudaStream_t side_stream(int dev, int k) {
     pool[dev][k] = nullptr;
   }
   return pool[dev][k];
+}
+
+std::mutex& batch_lock(int dev) {
+  static std::mutex locks[64];
+  return locks[dev < 0 || dev >= 64 ? 0 : dev];
 }
 
 // Orders `stream` after the work issued on the side streams (on every way
@@ -96,34 +118,65 @@ struct SideJoin {
   ~SideJoin() { join(); }
 };
 
-// Step s reads `in` (s = 0) or bufs[(first + s - 1) % 2] and writes `out`
-// (the last step) or bufs[(first + s) % 2].  When in, out and the plan's
-// scratch grid are all TMA-describable, bufs = {out, scratch} with the parity
-// `first` chosen so that the last step lands in out, and pitch = nx.
-// Otherwise (rows of nx floats are not a multiple of 16 bytes, or a buffer is
-// not 16-byte aligned) bufs are the plan's two padded grids with rows `pitch`
-// (nx rounded up to 4) floats apart, first = 0: every step but the first then
-// loads through TMA, and only the first step's halo boxes are loaded by the
-// consumers (`tma0` = 0).
+// A job runs in passes.  Pass p reads `in` (p = 0) or bufs[(first + p - 1)
+// % 2] and writes `out` (the last pass) or bufs[(first + p) % 2].  When in,
+// out and the plan's scratch grid are all TMA-describable, bufs = {out,
+// scratch} with the parity `first` chosen so that the last pass lands in out,
+// and pitch = nx.  Otherwise (rows of nx floats are not a multiple of 16
+// bytes, or a buffer is not 16-byte aligned) bufs are the plan's two padded
+// grids with rows `pitch` (nx rounded up to 4) floats apart, first = 0: every
+// pass but the first then loads through TMA, and only the first pass's halo
+// boxes are loaded by the consumers (`tma0` = 0).
+//
+// A job with `two` = 0 takes one step per pass on 64 x 128 tiles.  A job
+// with `two` = 1 takes two steps per pass on the fused kernel's tiles of
+// (64 - 2r) x 120 outputs: level 1, grown by r rows and 4 columns on each
+// side, goes to shared memory, level 2 to the grid, from one input box of
+// (64 + 2r) x 136 points -- the one-step box.  Its first pass takes a single
+// step when the step count is odd or the consumers load it (`head1`), and
+// its last a single step when what is left is odd (`tail1`), on the same
+// tiles.
 struct BatchJob {
   int64_t nx, ny;
   int64_t pitch;       // row pitch of bufs (floats)
   int r;
   int tiles_x, tiles_y;
-  int steps;
+  int steps;           // time steps of the run
+  int passes;          // passes of the run
+  int two;             // 1: two steps per pass on fused tiles
+  int head1, tail1;    // two: the first / last pass takes one step
+  int by, bx;          // output tile
   int first;
-  int map0;            // tensor maps: map0 + 0 = in, + 1 = bufs[0], + 2 = bufs[1]
+  int map0;            // tensor maps: map0 + 0 = in, + 1 = bufs[0], + 2 = bufs[1] (box of a full pass);
+                       // + 3 = in, + 4 = bufs[0], + 5 = bufs[1] (box of a one-step pass of a two-step job)
   const uint4* a;      // packed A operands (TF32, per A index)
   const uint32_t* meta;
   float* bufs[2];
   float* out;
   const float* in;
-  int* done;           // per-tile count of completed steps
-  int tma0;            // 1: `in` is TMA-describable; 0: consumers load the first step's boxes
+  int* done;           // per-tile count of completed passes
+  int tma0;            // 1: `in` is TMA-describable; 0: consumers load the first pass's boxes
 };
+
+// Steps of pass p of a job.
+__host__ __device__ inline int pass_steps(const BatchJob& jb, int p) {
+  if (!jb.two) return 1;
+  if (jb.head1 && p == 0) return 1;
+  if (jb.tail1 && p == jb.passes - 1) return 1;
+  return 2;
+}
 
 template <int R>
 using BatchTile = TileCfg<0, R, R, 1, kWarpsY, kWarpsX, kH>;
+// Two-step pass and one-step pass on the fused tile of radius R: the output
+// tile is (64 - 2R) x 120; level 1 of the two-step pass is 64 x 128.
+template <int R>
+using BatchFused2 = FuseCfg<R, 2, 64 - 2 * R, 120, 8, kWarpsY * kWarpsX>;
+template <int R>
+using BatchFused1 = FuseCfg<R, 1, 64 - 2 * R, 120, 8, kWarpsY * kWarpsX>;
+constexpr int kLevelFloats = 64 * 128;  // level 1 of a two-step pass (pitch 128)
+static_assert(BatchFused2<1>::kPStride == kLevelFloats * 4 && BatchFused2<3>::kPStride == kLevelFloats * 4,
+              "level buffer");
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -176,6 +229,53 @@ __device__ __forceinline__ void batch_tile(const BatchJob& jb, const uint4 (&A8)
         for (int c = 0; c < 2; ++c)
           if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * pitch + 8 * c] = acc[pp][2 * sr + c];
       }
+}
+
+// One pass of a two-step job on the fused tile at (x0, y0): STEPS = 2 runs
+// level 1 from the staged box into the shared level buffer P and level 2
+// into the grid; STEPS = 1 runs one level from the box into the grid.  The
+// consumer warps synchronise among themselves (named barrier 1), not with
+// the producer warps.
+template <int R, int STEPS, bool RIN>
+__device__ __forceinline__ void batch_fused(const BatchJob& jb, const uint4 (&A8)[kNA], const uint32_t (&E8)[kNA],
+                                            const float* S, float* P, float* dst, int64_t pitch, int x0, int y0,
+                                            bool out_tf32, int* status) {
+  using F = typename std::conditional<STEPS == 2, BatchFused2<R>, BatchFused1<R>>::type;
+  uint4 A[F::NA];
+  uint32_t E[F::NA];
+#pragma unroll
+  for (int a = 0; a < F::NA; ++a) {
+    A[a] = A8[a];
+    E[a] = E8[a];
+  }
+  uint4 Ad[F::NA][2];                        // unused in the sparse TF32 mode
+  uint4 Am[F::RY + 1];
+  uint32_t Em[F::RY + 1];
+  float W[(2 * F::RY + 1) * (2 * F::RX + 1)];
+  StepArgs args = {};
+  args.dst = dst;
+  args.nx = jb.nx;
+  args.ny = jb.ny;
+  args.nz = 1;
+  args.pitch = pitch;
+  args.status = status;
+  args.out_tf32 = out_tf32 ? 1 : 0;
+  FusedCtx c;
+  c.args = &args;
+  c.x0 = x0;
+  c.y0 = y0;
+  c.lane = threadIdx.x & 31;
+  c.warp = threadIdx.x >> 5;
+  c.g = c.lane >> 2;
+  c.q = c.lane & 3;
+  if constexpr (STEPS == 2) {
+    fused_level<F, Mode::SpTF32, RIN, 1>(c, S, P, A, E, Ad, Am, Em, W);
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // level 1 complete in P
+    fused_level<F, Mode::SpTF32, RIN, 2>(c, P, nullptr, A, E, Ad, Am, Em, W);
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // P is free for the next item
+  } else {
+    fused_level<F, Mode::SpTF32, RIN, 1>(c, S, nullptr, A, E, Ad, Am, Em, W);
+  }
 }
 
 // Warp-parallel search: the largest index i in [0, n) with table[i] <= key
@@ -241,7 +341,8 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
   uint64_t* empty = full + 2;
   ItemSlot* slot = reinterpret_cast<ItemSlot*>(empty + 2);
   volatile long long* claim_turn = reinterpret_cast<volatile long long*>(slot + 2);
-  unsigned char* tsm = smem + 2 * kStageStride + 128;
+  float* level = reinterpret_cast<float*>(smem + 2 * kStageStride + 128);  // level 1 of two-step items
+  unsigned char* tsm = smem + 2 * kStageStride + 128 + kLevelFloats * 4;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tables_in_smem) {
     const uint4* src = reinterpret_cast<const uint4*>(tables);
@@ -303,7 +404,7 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
       }
       // every consumer warp must have handed the stage back (use - 1); its
       // stores of that item are then ordered before this warp's release of
-      // the item's step counter (the fence waits here, not in the consumers)
+      // the item's pass counter (the fence waits here, not in the consumers)
       if (use > 0) {
         if (lane == 0) ok = mbar_wait_backoff(&empty[st], (uint32_t)((use - 1) & 1), status, 128, wait_cycles);
         if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
@@ -363,10 +464,13 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
         if (s > 0 || jb.tma0) {
           // the neighbours' generic-proxy stores must be visible to the TMA read
           asm volatile("fence.proxy.async.global;" ::: "memory");
-          const int src_map = jb.map0 + (s == 0 ? 0 : 1 + (jb.first + s - 1) % 2);
-          const uint32_t bytes = (uint32_t)((kBY + 2 * jb.r) * (kBX + 2 * kHaloX) * 4);
-          mbar_arrive_expect_tx(&full[st], bytes);
-          tma_load_3d(smem + st * kStageStride, &maps[src_map], &full[st], tx * kBX - kHaloX, ty * kBY - jb.r, 0);
+          // the pass's input box: the tile grown by r rows and 4 columns per step
+          const int np = pass_steps(jb, s);
+          const int bw = jb.bx + 2 * kHaloX * np, bh = jb.by + 2 * jb.r * np;
+          const int src_map = jb.map0 + ((jb.two && np == 1) ? 3 : 0) + (s == 0 ? 0 : 1 + (jb.first + s - 1) % 2);
+          mbar_arrive_expect_tx(&full[st], (uint32_t)(bw * bh * 4));
+          tma_load_3d(smem + st * kStageStride, &maps[src_map], &full[st], tx * jb.bx - kHaloX * np,
+                      ty * jb.by - jb.r * np, 0);
         } else {
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         }
@@ -405,18 +509,36 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
       cur_job = it.job;
     }
     const int tx = it.tile % jb.tiles_x, ty = it.tile / jb.tiles_x;
+    const int np = pass_steps(jb, it.s);
     float* Sw = reinterpret_cast<float*>(smem + st * kStageStride);
     if (it.s == 0 && !jb.tma0) {
-      load_box_async(jb.in, jb.nx, jb.ny, 1, (int64_t)tx * kBX - kHaloX, (int64_t)ty * kBY - jb.r, 0,
-                     kBX + 2 * kHaloX, kBY + 2 * jb.r, 1, Sw, warp, kThreads / 32, lane);
+      // a first pass of one step (head1 for two-step jobs)
+      load_box_async(jb.in, jb.nx, jb.ny, 1, (int64_t)tx * jb.bx - kHaloX, (int64_t)ty * jb.by - jb.r, 0,
+                     jb.bx + 2 * kHaloX, jb.by + 2 * jb.r, 1, Sw, warp, kThreads / 32, lane);
       asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
     }
     const float* S = Sw;
-    const bool last = it.s + 1 == jb.steps;
+    const bool last = it.s + 1 == jb.passes;
     float* dst = last ? jb.out : jb.bufs[(jb.first + it.s) % 2];
     const int64_t pitch = last ? jb.nx : jb.pitch;
     const bool out_tf32 = !last;
-    if (it.s == 0) {
+    if (jb.two) {
+      const int x0 = tx * jb.bx, y0 = ty * jb.by;
+#define SPIDER_BATCH_FUSED(R)                                                                          \
+  if (np == 2) {                                                                                       \
+    if (it.s == 0) batch_fused<R, 2, true>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);  \
+    else batch_fused<R, 2, false>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);          \
+  } else {                                                                                             \
+    if (it.s == 0) batch_fused<R, 1, true>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);  \
+    else batch_fused<R, 1, false>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);          \
+  }
+      switch (jb.r) {
+        case 1: SPIDER_BATCH_FUSED(1) break;
+        case 2: SPIDER_BATCH_FUSED(2) break;
+        default: SPIDER_BATCH_FUSED(3) break;
+      }
+#undef SPIDER_BATCH_FUSED
+    } else if (it.s == 0) {
       switch (jb.r) {
         case 1: batch_tile<1, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
         case 2: batch_tile<2, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
@@ -448,6 +570,15 @@ extern "C" spider_status spider_set_wait_limit(long long cycles) {
   return SPIDER_OK;
 }
 
+extern "C" spider_status spider_batch_configure(long long fuse_min_points, int queue_steps_per_item) {
+  set_error("");
+  if (fuse_min_points < 0 || queue_steps_per_item < 0 || queue_steps_per_item > 2)
+    return fail(SPIDER_ERR_INVALID, "fuse_min_points >= 0, queue_steps_per_item 0..2");
+  g_fuse_min_points.store(fuse_min_points > 0 ? fuse_min_points : kFuseMinPoints);
+  g_queue_steps.store(queue_steps_per_item > 0 ? queue_steps_per_item : kQueueStepsPerItem);
+  return SPIDER_OK;
+}
+
 extern "C" spider_status spider_batch_drop_item(long long item) {
   set_error("");
   if (item < -1) return fail(SPIDER_ERR_INVALID, "item must be >= -1");
@@ -471,6 +602,11 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return fail(SPIDER_ERR_INVALID, "a plan may appear once per batch (its scratch grid)");
   }
+  int batch_dev = 0;
+  if (cudaGetDevice(&batch_dev) != cudaSuccess) return fail(SPIDER_ERR_CUDA, "cudaGetDevice");
+  std::lock_guard<std::mutex> whole_call(batch_lock(batch_dev));
+  const long long fuse_min_points = g_fuse_min_points.load();
+  const bool two_step_items = g_queue_steps.load() == 2;
   // Jobs the persistent queue handles: 2-D sparse TF32, radius <= 3, at
   // least one step, and fewer than kFuseMinPoints points.  Larger grids of
   // several steps run as fused multi-step passes of their own (the plan's
@@ -483,7 +619,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     spider_plan_t* p = plans[i];
     const bool ok = p->ndim == 2 && p->r <= kMaxR && p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec == SPIDER_TF32 &&
                     steps[i] > 0;
-    const bool big = ok && steps[i] > 1 && p->points() >= kFuseMinPoints;
+    const bool big = ok && steps[i] > 1 && p->points() >= fuse_min_points;
     (big ? fused : ok ? queued : direct).push_back(i);
   }
   // The fused grids run on side streams (after the work already on
@@ -528,10 +664,10 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
   if (!queued.empty()) {
     const int nq = (int)queued.size();
     std::vector<BatchJob> jobs(nq);
-    std::vector<CUtensorMap> maps(3 * (size_t)nq);
+    std::vector<CUtensorMap> maps(6 * (size_t)nq);
     std::vector<long long> tiles(nq);
     long long total_tiles = 0;
-    int max_steps = 0;
+    int max_steps = 0;  // the longest job's passes: queue items are (pass, job, tile)
     for (int k = 0; k < nq; ++k) {
       const int i = queued[k];
       spider_plan_t* p = plans[i];
@@ -542,59 +678,83 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       jb.nx = p->nx;
       jb.ny = p->ny;
       jb.r = p->r;
-      jb.tiles_x = (int)((p->nx + kBX - 1) / kBX);
-      jb.tiles_y = (int)((p->ny + kBY - 1) / kBY);
       jb.steps = (int)steps[i];
-      jb.map0 = 3 * k;
+      // two steps per pass on the fused tile for jobs of several steps
+      jb.two = (steps[i] > 1 && two_step_items) ? 1 : 0;
+      jb.by = jb.two ? 64 - 2 * p->r : kBY;
+      jb.bx = jb.two ? 120 : kBX;
+      jb.tiles_x = (int)((p->nx + jb.bx - 1) / jb.bx);
+      jb.tiles_y = (int)((p->ny + jb.by - 1) / jb.by);
+      jb.map0 = 6 * k;
       jb.a = reinterpret_cast<const uint4*>(p->dev.a_words);
       jb.meta = p->dev.meta_words;
       jb.out = outs[i];
       jb.in = ins[i];
       jb.done = nullptr;
+      // boxes: a full pass reads (by + 2r T) x (bx + 8 T) with T = 1 (one-step
+      // tiles) or 2 (fused tiles), both (64 + 2r) x 136; a one-step pass of a
+      // two-step job reads (by + 2r) x (bx + 8) = 64 x 128
       const int box_x = kBX + 2 * kHaloX, box_y = kBY + 2 * p->r;
-      CUtensorMap* mp = &maps[3 * k];
-      std::memset(mp, 0, 3 * sizeof(CUtensorMap));
+      const int box1_x = 128, box1_y = 64;
+      CUtensorMap* mp = &maps[6 * k];
+      std::memset(mp, 0, 6 * sizeof(CUtensorMap));
       jb.tma0 = make_tensor_map(&mp[0], ins[i], p->nx, p->ny, 1, box_x, box_y, 1) ? 1 : 0;
+      if (jb.tma0 && jb.two) make_tensor_map(&mp[3], ins[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
+      if (jb.two) {
+        jb.head1 = (jb.steps % 2 == 1 || !jb.tma0) ? 1 : 0;
+        jb.tail1 = ((jb.steps - jb.head1) % 2 == 1) ? 1 : 0;
+        jb.passes = jb.head1 + (jb.steps - jb.head1 - jb.tail1) / 2 + jb.tail1;
+      } else {
+        jb.head1 = jb.tail1 = 0;
+        jb.passes = jb.steps;
+      }
       const bool direct = jb.tma0 && make_tensor_map(&mp[1], outs[i], p->nx, p->ny, 1, box_x, box_y, 1) &&
-                          (steps[i] == 1 ||
+                          (jb.passes == 1 ||
                            make_tensor_map(&mp[2], p->dev.scratch, p->nx, p->ny, 1, box_x, box_y, 1));
       if (direct) {
         jb.pitch = p->nx;
-        jb.first = (steps[i] % 2 == 1) ? 0 : 1;
+        jb.first = (jb.passes % 2 == 1) ? 0 : 1;
         jb.bufs[0] = outs[i];
         jb.bufs[1] = p->dev.scratch;
-        if (steps[i] == 1) mp[2] = mp[0];
+        if (jb.passes == 1) mp[2] = mp[0];
+        if (jb.two) {
+          make_tensor_map(&mp[4], outs[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
+          if (jb.passes > 1) make_tensor_map(&mp[5], p->dev.scratch, p->nx, p->ny, 1, box1_x, box1_y, 1);
+        }
       } else {
         jb.pitch = (p->nx + 3) / 4 * 4;
         jb.first = 0;
         jb.bufs[0] = jb.bufs[1] = nullptr;
-        if (steps[i] > 1) {
+        if (jb.passes > 1) {
           const size_t grid_bytes = (size_t)jb.pitch * (size_t)p->ny * 4;
           st = ensure_plan_pad(p, 2 * grid_bytes);
           if (st != SPIDER_OK) return st;
           jb.bufs[0] = p->dev.pad;
           jb.bufs[1] = p->dev.pad + grid_bytes / 4;
-          for (int m = 0; m < 2; ++m)
-            if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box_x, box_y, 1))
+          for (int m = 0; m < 2; ++m) {
+            if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box_x, box_y, 1) ||
+                (jb.two &&
+                 !make_tensor_map_pitched(&mp[4 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box1_x, box1_y, 1)))
               return fail(SPIDER_ERR_CUDA, "tensor map of a padded grid");
+          }
         }
-        if (!jb.tma0) mp[0] = steps[i] > 1 ? mp[1] : mp[0];  // unused: the consumers load step 0
+        if (!jb.tma0) mp[0] = jb.passes > 1 ? mp[1] : mp[0];  // unused: the consumers load pass 0
       }
       tiles[k] = (long long)jb.tiles_x * jb.tiles_y;
       total_tiles += tiles[k];
-      max_steps = std::max(max_steps, jb.steps);
+      max_steps = std::max(max_steps, jb.passes);
     }
-    // order jobs by descending step count: the jobs active at step s are a prefix
+    // order jobs by descending pass count: the jobs active at pass s are a prefix
     std::vector<int> order(nq);
     for (int k = 0; k < nq; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].steps > jobs[b].steps; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].passes > jobs[b].passes; });
     std::vector<long long> tile_prefix(nq + 1, 0);
     for (int k = 0; k < nq; ++k) tile_prefix[k + 1] = tile_prefix[k] + tiles[order[k]];
     std::vector<int> active(max_steps);
     std::vector<long long> step_off(max_steps + 1, 0);
     for (int s = 0; s < max_steps; ++s) {
       int c = 0;
-      while (c < nq && jobs[order[c]].steps > s) ++c;
+      while (c < nq && jobs[order[c]].passes > s) ++c;
       active[s] = c;
       step_off[s + 1] = step_off[s] + tile_prefix[c];
     }
@@ -665,7 +825,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     const int grid = (int)std::max<long long>(
         1, std::min({total_items, widest_step, (long long)std::max(occ, 1) * device_sm_count()}));
     // The persistent launch is issued as a CUDA graph: the work-queue reset
-    // (counter and per-tile step counters) and the kernel, launched on the
+    // (counter and per-tile pass counters) and the kernel, launched on the
     // caller's stream.
     const unsigned char* a_tables = dev;
     int a_tbytes = (int)tables_bytes, a_tsm = tables_in_smem, a_oo = (int)o_order, a_os = (int)o_step,

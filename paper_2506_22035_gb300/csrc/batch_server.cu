@@ -21,9 +21,10 @@
 //    never stall the launches of the other jobs.
 // A job's arithmetic does not depend on what else runs: the result is the
 // same as a lone spider_run of the same plan in the arithmetic chosen for
-// it.  The arithmetic is the fastest whose a priori error bound
-// (spider_plan_error_bound) meets the job's error target: sparse TF32, then
-// the FP16 hi/lo split, then FP32 on CUDA cores.
+// it.  The arithmetic is, among those whose a priori error bound
+// (spider_plan_error_bound) meets the job's error target, the one measured
+// fastest for the job's class of stencil (sparse TF32, the FP16 hi/lo split,
+// FP32 on CUDA cores), run with fused time steps where they are built.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -52,6 +53,9 @@ struct Job {
   uint64_t ticket = 0;
   spider_plan plan = nullptr;
   double bound = 0;         // a priori error bound of the chosen arithmetic
+  spider_precision prec = SPIDER_TF32;
+  spider_engine engine = SPIDER_ENGINE_SPARSE_TC;
+  int steps_per_pass = 1;
   int64_t steps = 0, done_steps = 0;
   std::unique_ptr<float[]> host;  // input at submit, result when done
   size_t npts = 0;
@@ -101,6 +105,30 @@ size_t job_bytes(const spider_plan_t* p) {
   size_t b = 3 * (size_t)p->points() * sizeof(float) + 65536;
   if (p->ndim >= 2 && p->nx % 4 != 0) b += 2 * (size_t)((p->nx + 3) / 4 * 4) * p->ny * p->nz * sizeof(float);
   return b;
+}
+
+// Measured speed of the arithmetics per stencil class (GStencil/s on one
+// GB300, autotuned, 2048^2 2-D and 160^3 3-D grids of U[0,1) values), used
+// to rank the arithmetics whose error bound meets a job's target, and the
+// steps per pass / tile variant the autotuner chose there.  FP32 on CUDA
+// cores beats the FP16 split for radius 1 and 3-D radius 2; the split wins
+// for larger 2-D stencils and 3-D radius 3.
+struct ClassRate {
+  double tf32, f16x2, cuda_core;
+  int t_tf32, v_tf32, t_f16, v_f16, t_cc, v_cc;
+};
+ClassRate class_rate(const spider_plan_t* p) {
+  const int r = std::min(p->r, kMaxR);
+  if (p->ndim == 3) {
+    static const ClassRate k3[3] = {{245, 140, 165, 1, 0, 1, 0, 1, 0},
+                                    {165, 64, 76, 1, 0, 1, 0, 1, 0},
+                                    {117, 35, 30, 1, 0, 1, 0, 1, 0}};
+    return k3[r - 1];
+  }
+  static const ClassRate k2[3] = {{998, 636, 731, 3, 3, 2, 4, 2, 4},
+                                  {809, 494, 477, 2, 3, 2, 3, 1, 0},
+                                  {699, 400, 331, 2, 0, 3, 1, 1, 0}};
+  return k2[r - 1];
 }
 
 // Copies n floats, a few threads for large grids (one host thread copies at
@@ -396,17 +424,37 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
   std::unique_ptr<float[]> host(new (std::nothrow) float[npts]);
   if (!host) return fail(SPIDER_ERR_OOM, "host copy of the job's grid");
   const float amax = copy_and_max_abs(host.get(), host_in, npts);
-  struct Choice { spider_precision prec; spider_engine engine; };
-  std::vector<Choice> choices = {{plan->prec, plan->engine}, {SPIDER_TF32, SPIDER_ENGINE_SPARSE_TC}};
-  if (amax < 16384.f) choices.push_back({SPIDER_F16X2, SPIDER_ENGINE_SPARSE_TC});
-  choices.push_back({SPIDER_TF32, SPIDER_ENGINE_CUDA_CORE});
+  // among the arithmetics whose a priori bound meets the target, the one
+  // measured fastest for this class of stencil; the caller's own plan
+  // settings when they meet it
+  struct Choice { spider_precision prec; spider_engine engine; double rate; };
+  const ClassRate cr = class_rate(plan);
+  std::vector<Choice> choices = {{SPIDER_TF32, SPIDER_ENGINE_SPARSE_TC, cr.tf32},
+                                 {SPIDER_TF32, SPIDER_ENGINE_CUDA_CORE, cr.cuda_core}};
+  if (amax < 16384.f) choices.push_back({SPIDER_F16X2, SPIDER_ENGINE_SPARSE_TC, cr.f16x2});
   int pick = -1;
   double bound = 0;
-  for (size_t k = 0; k < choices.size() && pick < 0; ++k) {
-    const ErrorModel m = error_model(plan, choices[k].prec, choices[k].engine);
-    if (!m.built) continue;
-    bound = (double)steps * (m.wsum + m.drift) + m.floor;
-    if (bound <= err_target) pick = (int)k;
+  {
+    const ErrorModel own = error_model(plan, plan->prec, plan->engine);
+    const double b = (double)steps * (own.wsum + own.drift) + own.floor;
+    if (own.built && b <= err_target) {
+      choices.insert(choices.begin(), {plan->prec, plan->engine, 1e30});
+      pick = 0;
+      bound = b;
+    }
+  }
+  if (pick < 0) {
+    double best = -1;
+    for (size_t k = 0; k < choices.size(); ++k) {
+      const ErrorModel m = error_model(plan, choices[k].prec, choices[k].engine);
+      if (!m.built) continue;
+      const double b = (double)steps * (m.wsum + m.drift) + m.floor;
+      if (b <= err_target && choices[k].rate > best) {
+        best = choices[k].rate;
+        pick = (int)k;
+        bound = b;
+      }
+    }
   }
   if (pick < 0)
     return fail(SPIDER_ERR_UNSUPPORTED, "no arithmetic built for this stencil meets the error target");
@@ -421,11 +469,24 @@ spider_status spider_submit(spider_server s, spider_plan plan, const float* host
       return st;
     }
   }
-  copy->steps_per_pass = std::min(plan->steps_per_pass, max_steps_per_pass(copy));
-  copy->tile_variant = plan->tile_variant;
+  // fused passes: the caller's setting, else the autotuner's choice for
+  // this kind of stencil if one was measured in this process, else the
+  // class's measured choice
+  int T = plan->steps_per_pass, v = plan->tile_variant;
+  if (T <= 1 && !autotune_lookup(copy, &T, &v)) {
+    const bool tf32 = copy->engine == SPIDER_ENGINE_SPARSE_TC && copy->prec == SPIDER_TF32;
+    const bool f16 = copy->engine == SPIDER_ENGINE_SPARSE_TC && copy->prec == SPIDER_F16X2;
+    T = tf32 ? cr.t_tf32 : f16 ? cr.t_f16 : copy->engine == SPIDER_ENGINE_CUDA_CORE ? cr.t_cc : 1;
+    v = tf32 ? cr.v_tf32 : f16 ? cr.v_f16 : copy->engine == SPIDER_ENGINE_CUDA_CORE ? cr.v_cc : 0;
+  }
+  copy->steps_per_pass = std::max(1, std::min(T, max_steps_per_pass(copy)));
+  copy->tile_variant = v;
   auto j = std::make_unique<Job>();
   j->plan = copy;
   j->bound = bound;
+  j->prec = copy->prec;
+  j->engine = copy->engine;
+  j->steps_per_pass = copy->steps_per_pass;
   j->steps = steps;
   j->reserve = job_bytes(copy);
   if (j->reserve > s->budget) {
@@ -468,6 +529,21 @@ spider_status spider_poll(spider_server s, uint64_t ticket, float* out, int* don
     if (j->status != SPIDER_OK) return fail(j->status, j->error);
   }
   if (owned && out) parallel_copy(out, owned->host.get(), (int64_t)owned->npts);
+  return SPIDER_OK;
+}
+
+spider_status spider_server_job_arithmetic(spider_server s, uint64_t ticket, spider_precision* prec,
+                                          spider_engine* engine, int* steps_per_pass, double* bound) {
+  set_error("");
+  if (!s) return fail(SPIDER_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return fail(SPIDER_ERR_INVALID, "unknown ticket");
+  const Job* j = it->second.get();
+  if (prec) *prec = j->prec;
+  if (engine) *engine = j->engine;
+  if (steps_per_pass) *steps_per_pass = j->steps_per_pass;
+  if (bound) *bound = j->bound;
   return SPIDER_OK;
 }
 

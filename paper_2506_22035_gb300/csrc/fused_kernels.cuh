@@ -47,7 +47,10 @@ struct FuseCfg {
   static constexpr int kPStride = T >= 2 ? align1k(rows(1) * pitch(1) * 4) : 0;  // odd levels
   static constexpr int kQStride = T >= 3 ? align1k(rows(2) * pitch(2) * 4) : 0;  // even levels
   static constexpr int kSmemBytes = kInStages * kInStride + kPStride + kQStride + 1024 + 64;
-  static_assert(T >= 2, "use the one-step kernel for T = 1");
+  // T = 1 describes a one-level pass on a fused tile's geometry (the batch
+  // queue's single-step passes of a job that otherwise takes two steps per
+  // pass); the stand-alone fused kernel is launched for T >= 2 only
+  static_assert(T >= 1, "at least one level");
   static_assert(BX % 8 == 0 && BX >= 64, "tile width");
   static_assert(width(0) <= 256 && rows(0) <= 256, "TMA box dimension limit");
   static_assert(H % 2 == 0 && rows(T) >= H, "warp tile height");

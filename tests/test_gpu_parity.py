@@ -649,23 +649,6 @@ def test_batch_with_direct_jobs_and_precisions():
         p.close()
 
 
-def server_choice(plan, u0, steps, err):
-    """The arithmetic spider_submit picks: the first of (the plan's own, sparse
-    TF32, FP16 hi/lo if every |value| < 16384, FP32 on CUDA cores) whose a
-    priori bound meets the target."""
-    cands = [(plan.precision, plan.engine), ("tf32", "sparse_tc")]
-    if np.max(np.abs(u0)) < 16384:
-        cands.append(("f16x2", "sparse_tc"))
-    cands.append(("tf32", "cuda_core"))
-    for prec, eng in cands:
-        try:
-            if plan.error_bound(steps, prec, eng) <= err:
-                return prec, eng
-        except spider.SpiderError:
-            continue
-    return None
-
-
 def test_server_results_same_alone_and_in_the_mix():
     import time
     g = np.random.default_rng(9)
@@ -690,21 +673,24 @@ def test_server_results_same_alone_and_in_the_mix():
         if t is None:
             continue
         assert t in shape_of and t not in results
+        arith = server.arithmetic(t)             # before poll releases the record
         out = np.empty(shape_of[t], np.float32)
         done, lat = server.poll(t, out)
         assert done
-        results[t] = (out, lat)
+        results[t] = (out, lat, arith)
     assert len(results) == len(tickets)
     assert server.wait(0.0) is None
     picked = set()
     for t, p, (u0, w, kind, steps, err) in zip(tickets, plans, jobs):
-        out, lat = results[t]
+        out, lat, (prec, eng, T, bound) = results[t]
         assert lat > 0
-        prec, eng = server_choice(p, u0, steps, err)
+        # the arithmetic's own bound meets the target, and the measurement the bound
+        assert bound <= err and abs(p.error_bound(steps, prec, eng) - bound) <= 1e-12 * bound
         picked.add((prec, eng))
         ref = oracle.stencil(u0, w, steps)
         rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
         assert rel <= err, (u0.shape, steps, err, prec, eng, rel)   # the job's own error target
+        assert rel <= bound
         # the server advances jobs in chunks of steps, in the arithmetic it
         # picked: the same results as a lone run in that arithmetic
         alone = gpu_run(u0, w, steps, kind, prec, eng)
