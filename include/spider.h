@@ -313,7 +313,8 @@ spider_status spider_batch_configure(long long fuse_min_points, int queue_steps_
  *
  * spider_batch_drop_item: a test hook.  The next spider_batch call leaves
  * item `item` of its persistent queue out (items numbered in the queue's
- * pass-major order, from 0; -1 clears): the item is claimed but neither
+ * queue's order, from 0: the first items are pass 0 of every job, jobs of
+ * more passes first, tiles row by row; -1 clears): the item is claimed but neither
  * loaded nor computed, and its tile's pass counter is not advanced, so the
  * items that depend on it wait until the limit runs out and the call returns
  * SPIDER_ERR_TIMEOUT (that call's results are then undefined).  The hook

@@ -2,7 +2,7 @@
 
 Every wait in the library's kernels is bounded.  The failure is made on the
 host: spider_batch_drop_item leaves one work item of the persistent batch
-queue out, so the items of the next step that need that tile wait for a step
+queue out, so the items of the next pass that need that tile wait for a pass
 counter that never advances.  With a short wait limit the kernel records a
 timeout and finishes; spider_batch must report SPIDER_ERR_TIMEOUT, and the
 device, the plans and the library must stay usable: the next ordinary calls
@@ -27,8 +27,8 @@ DEFAULT_LIMIT = 4_000_000_000
 def test_dropped_queue_item_times_out_and_the_device_stays_usable():
     lib = _native.load()
     g = si.rng(70, 0)
-    # 200 x 320 points (< 2^16): the persistent queue takes it, 3 x 4 tiles
-    # of 64 x 128 per step, items 0..11 are step 0
+    # 200 x 320 points (< 2^16): the persistent queue takes it, 4 x 3 tiles
+    # of 62 x 120 per pass of two steps, items 0..11 are pass 0
     u0 = si.grid((200, 320), -1, 1, g)
     w = si.normalised_coeffs(2, 1, "box", si.rng(70, 1))
     steps = 6
@@ -37,7 +37,7 @@ def test_dropped_queue_item_times_out_and_the_device_stays_usable():
     b = torch.full_like(a, float("nan"))
     try:
         _native.check(lib.spider_set_wait_limit(200_000), "spider_set_wait_limit")   # ~0.1 ms
-        _native.check(lib.spider_batch_drop_item(5), "spider_batch_drop_item")        # step 0, tile (1, 2)
+        _native.check(lib.spider_batch_drop_item(5), "spider_batch_drop_item")        # pass 0, tile (2, 1)
         with pytest.raises(spider.SpiderError) as ei:
             spider.batch([plan], [a], [b], [steps])
         assert ei.value.status == SPIDER_ERR_TIMEOUT

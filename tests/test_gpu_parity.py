@@ -587,6 +587,30 @@ def test_batch_persistent_queue_matches_individual_runs():
         p.close()
 
 
+@pytest.mark.parametrize("fuse_min_points,queue_steps", [(1 << 40, 1), (1 << 40, 2), (1 << 10, 2)])
+def test_batch_routes_match_individual_runs(fuse_min_points, queue_steps):
+    # every grid in the persistent queue (one or two steps per item), or
+    # almost every grid as fused passes on side streams: the same results,
+    # bit for bit, as each plan's own run
+    jobs = _batch_jobs()
+    plans, ins, outs, refs = [], [], [], []
+    for u0, w, kind, steps in jobs:
+        plans.append(spider.Plan(w, u0.shape, kind, "tf32"))
+        ins.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.full_like(ins[-1], float("nan")))
+        refs.append(gpu_run(u0, w, steps, kind, "tf32"))
+    try:
+        spider.batch_configure(fuse_min_points, queue_steps)
+        spider.batch(plans, ins, outs, [j[3] for j in jobs])
+        torch.cuda.synchronize()
+    finally:
+        spider.batch_configure(0, 0)
+    for k in range(len(jobs)):
+        assert np.array_equal(outs[k].cpu().numpy(), refs[k]), k
+    for p in plans:
+        p.close()
+
+
 def _offset_view(t, off):
     """A copy of `t` that starts `off` floats into its own allocation (a base
     address that is not 16-byte aligned when off % 4 != 0)."""
