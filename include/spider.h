@@ -281,7 +281,10 @@ void spider_plan_destroy(spider_plan plan);
  * engines, radius above 3) run through spider_run on the same stream after
  * the persistent launch.  Grids whose rows are not a multiple of 4 floats,
  * or whose buffers are not 16-byte aligned, use the plan's padded grids (see
- * spider_run).  Synchronous: returns when all grids are done.  n <= 4096.
+ * spider_run).  A call whose queued grids are those of the previous call on
+ * the device (same plans, buffers, step counts and routing) relaunches that
+ * call's persistent launch as it was built, without rebuilding or uploading
+ * its tables.  Synchronous: returns when all grids are done.  n <= 4096.
  * Concurrent calls on one device (other threads or streams) run one after
  * another: they share the library's side streams and work queue.
  * SPIDER_ERR_TIMEOUT if a dependency wait ran out. */

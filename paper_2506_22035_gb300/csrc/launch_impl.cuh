@@ -207,12 +207,13 @@ cudaError_t launch_class(int cls, const LaunchCtx& ctx) {
   if (cls == 1) return launch_cfg<TileCfg<0, 0, R, 1, 1, 2, 2>, MODE>(ctx);
   if (cls == 2) return launch_cfg<TileCfg<0, R, R, 1, 4, 2, 16>, MODE>(ctx);
   if (cls == 3) {
-    // TF32 star stencils skip the zero operands of the off-centre planes
-    if constexpr (is_tf32_mode(MODE)) {
+    // star stencils skip the zero operands of the off-centre planes (the
+    // cube tiles, for grids TMA cannot read, in TF32 only)
+    if constexpr (MODE != Mode::CudaCore) {
       if (ctx.plan->shape == SPIDER_STAR) {
         const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE, true>(ctx);
         if (e != cudaErrorNotSupported) return e;
-        return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE, true>(ctx);
+        if constexpr (is_tf32_mode(MODE)) return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE, true>(ctx);
       }
     }
     const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE>(ctx);

@@ -224,40 +224,58 @@ __device__ __forceinline__ void mma_k32(float (&d)[4], const uint4& a, uint32_t 
   else mma_sp_f16_k32(d, a, e, b0, b1, b2, b3);
 }
 
-template <class C, bool BF16, int PASS, int SP, int JJ>
+// Whether rows JJ, JJ + 1 (JJ even) feed a two-row combo (a0, a0 + 1),
+// a0 = JJ - 2pp, that touches the applied A indices AMIN..AMAX.
+template <class C, int AMIN, int AMAX>
+__host__ __device__ constexpr bool split_rows_needed(int jj) {
+  for (int pp = 0; pp < C::H / 2; ++pp) {
+    const int a0 = jj - 2 * pp;
+    if (a0 >= 0 && a0 + 1 < C::NA && a0 <= AMAX && a0 + 1 >= AMIN) return true;
+  }
+  return false;
+}
+
+// Only the A indices AMIN..AMAX are applied (all by default; a 3-D star's
+// off-centre planes apply ry, ry + 1): a two-row combo runs when one of its
+// two kernel rows is applied (the other one is zero in the packed operand),
+// a cross combo only for an applied index, and rows no combo reads are not
+// loaded.
+template <class C, bool BF16, int PASS, int SP, int JJ, int AMIN, int AMAX>
 __device__ __forceinline__ void sp_split_rows(uint32_t addr, const uint4 (&Am)[C::RY + 1],
                                               const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
                                               const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
                                               float (&accC)[C::H / 2][4]) {
-  uint32_t t0[2], c0[2], h0[2], t1[2], c1[2], h1[2];
-  split_terms<BF16, PASS>(lds128_at<JJ * SP * 4>(addr), t0, c0, h0);
-  split_terms<BF16, PASS>(lds128_at<(JJ + 1) * SP * 4>(addr), t1, c1, h1);
+  if constexpr (split_rows_needed<C, AMIN, AMAX>(JJ)) {
+    uint32_t t0[2], c0[2], h0[2], t1[2], c1[2], h1[2];
+    split_terms<BF16, PASS>(lds128_at<JJ * SP * 4>(addr), t0, c0, h0);
+    split_terms<BF16, PASS>(lds128_at<(JJ + 1) * SP * 4>(addr), t1, c1, h1);
 #pragma unroll
-  for (int pp = 0; pp < C::H / 2; ++pp) {
-    const int a0 = JJ - 2 * pp;  // even; rows JJ, JJ+1 use A indices a0, a0+1
-    if (a0 >= 0 && a0 + 1 < C::NA) {
-      if (PASS == 0) {
-        float f[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_k32<C, BF16>(f, Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
+    for (int pp = 0; pp < C::H / 2; ++pp) {
+      const int a0 = JJ - 2 * pp;  // even; rows JJ, JJ+1 use A indices a0, a0+1
+      if (a0 >= 0 && a0 + 1 < C::NA && a0 <= AMAX && a0 + 1 >= AMIN) {
+        if (PASS == 0) {
+          float f[4] = {0.f, 0.f, 0.f, 0.f};
+          mma_k32<C, BF16>(f, Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) accM[pp][i] += f[i];
-      } else {
-        mma_k32<C, BF16>(accC[pp], Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
+          for (int i = 0; i < 4; ++i) accM[pp][i] += f[i];
+        } else {
+          mma_k32<C, BF16>(accC[pp], Am[a0 / 2], Em[a0 / 2], t0[0], t0[1], t1[0], t1[1]);
+        }
+        if (a0 >= AMIN) mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], c0[0], c0[1], h0[0], h0[1]);
+        if (a0 + 1 <= AMAX) mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], c1[0], c1[1], h1[0], h1[1]);
       }
-      mma_k32<C, BF16>(accC[pp], Ac[a0], Ec[a0], c0[0], c0[1], h0[0], h0[1]);
-      mma_k32<C, BF16>(accC[pp], Ac[a0 + 1], Ec[a0 + 1], c1[0], c1[1], h1[0], h1[1]);
     }
   }
   if constexpr (JJ + 2 < C::H + 2 * C::RY)
-    sp_split_rows<C, BF16, PASS, SP, JJ + 2>(addr, Am, Em, Ac, Ec, accM, accC);
+    sp_split_rows<C, BF16, PASS, SP, JJ + 2, AMIN, AMAX>(addr, Am, Em, Ac, Ec, accM, accC);
 }
 
-template <class C, bool BF16, int PASS = 0, int SP = C::SX>
+template <class C, bool BF16, int PASS = 0, int SP = C::SX, int AMIN = 0, int AMAX = C::NA - 1>
 __device__ __forceinline__ void plane_sp_split(const float* row0, const uint4 (&Am)[C::RY + 1],
                                                const uint32_t (&Em)[C::RY + 1], const uint4 (&Ac)[C::NA],
                                                const uint32_t (&Ec)[C::NA], float (&accM)[C::H / 2][4],
                                                float (&accC)[C::H / 2][4]) {
-  sp_split_rows<C, BF16, PASS, SP, 0>(smem_u32(row0), Am, Em, Ac, Ec, accM, accC);
+  sp_split_rows<C, BF16, PASS, SP, 0, AMIN, AMAX>(smem_u32(row0), Am, Em, Ac, Ec, accM, accC);
 }
 
 // Packed combos of one pass of a split precision: (RY + 1) two-row combos,
@@ -280,22 +298,22 @@ __device__ __forceinline__ void load_split_operands(const StepArgs& args, int fi
 
 // The whole split product of one dz plane (index dzi) into accM / accC:
 // FP16 one pass with the operands already in registers; BF16 two passes,
-// each loading its operands first.
-template <class C, Mode MODE, int SP = C::SX>
+// each loading its operands first.  AMIN..AMAX: the applied A indices.
+template <class C, Mode MODE, int SP = C::SX, int AMIN = 0, int AMAX = C::NA - 1>
 __device__ __forceinline__ void plane_split(const StepArgs& args, int dzi, int lane, const float* row0,
                                             uint4 (&Am)[C::RY + 1], uint32_t (&Em)[C::RY + 1], uint4 (&A)[C::NA],
                                             uint32_t (&E)[C::NA], float (&accM)[C::H / 2][4],
                                             float (&accC)[C::H / 2][4]) {
   constexpr int kPass = (C::RY + 1) + C::NA;
   if (MODE == Mode::SpF16x2) {
-    plane_sp_split<C, false, 0, SP>(row0, Am, Em, A, E, accM, accC);
+    plane_sp_split<C, false, 0, SP, AMIN, AMAX>(row0, Am, Em, A, E, accM, accC);
   } else {
     // a loop the compiler keeps: one pass's operands live at a time
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       load_split_operands<C>(args, (2 * dzi + pass) * kPass, lane, Am, Em, A, E);
-      if (pass == 0) plane_sp_split<C, true, 0, SP>(row0, Am, Em, A, E, accM, accC);
-      else plane_sp_split<C, true, 1, SP>(row0, Am, Em, A, E, accM, accC);
+      if (pass == 0) plane_sp_split<C, true, 0, SP, AMIN, AMAX>(row0, Am, Em, A, E, accM, accC);
+      else plane_sp_split<C, true, 1, SP, AMIN, AMAX>(row0, Am, Em, A, E, accM, accC);
     }
   }
 }

@@ -58,8 +58,11 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
   constexpr int CPP = MODE == Mode::SpF16x2 ? (C::RY + 1) + NA : NA;
   constexpr int NZ = 2 * C::RZ + 1;
   constexpr int NWT = (2 * C::RY + 1) * (2 * C::RX + 1);
-  // operands: all dz planes (small stencils) or one plane at a time
-  constexpr int NPL = C::kAllOperands ? NZ : 1;
+  // operands: all dz planes (small TF32 stencils) or one plane at a time;
+  // the FP16 split keeps one plane's (its 32 accumulators leave no room for
+  // three planes' operands at two or more CTAs per SM)
+  constexpr bool kAll = C::kAllOperands && MODE != Mode::SpF16x2;
+  constexpr int NPL = kAll ? NZ : 1;
   uint4 A[NPL][NA];
   uint32_t E[NPL][NA];
   uint4 Ad[NPL][NA][2];
@@ -82,7 +85,23 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
         Ad[k][a][1] = args.a_words[((size_t)(dzi * NA + a) * 32 + lane) * 2 + 1];
       }
     } else if (MODE == Mode::SpF16x2) {
-      load_split_operands<C>(args, dzi * CPP, lane, Am[k], Em[k], A[k], E[k]);
+      if (STAR && dzi != C::RZ) {
+        // off-centre plane of a star: the two-row combos and the cross
+        // combos of A indices ry, ry + 1 (the others are zero and not applied)
+#pragma unroll
+        for (int c = 0; c <= C::RY; ++c) {
+          if (2 * c + 1 < C::RY || 2 * c > C::RY + 1) continue;
+          Am[k][c] = args.a_words[(size_t)(dzi * CPP + c) * 32 + lane];
+          Em[k][c] = args.meta[(size_t)(dzi * CPP + c) * 32 + lane];
+        }
+#pragma unroll
+        for (int a = C::RY; a <= C::RY + 1; ++a) {
+          A[k][a] = args.a_words[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
+          E[k][a] = args.meta[(size_t)(dzi * CPP + C::RY + 1 + a) * 32 + lane];
+        }
+      } else {
+        load_split_operands<C>(args, dzi * CPP, lane, Am[k], Em[k], A[k], E[k]);
+      }
     } else if (MODE == Mode::SpBF16x3) {
       // two passes of operands, loaded by plane_split
     } else {
@@ -90,7 +109,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
       for (int i = 0; i < NWT; ++i) W[i] = args.w[(size_t)dzi * NWT + i];
     }
   };
-  if (C::kAllOperands) {
+  if (kAll) {
 #pragma unroll
     for (int dzi = 0; dzi < NZ; ++dzi) load_operands(dzi, dzi);
   }
@@ -142,9 +161,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
         for (int i = 0; i < C::H; ++i) acc[i][0] = acc[i][1] = 0.f;
 #pragma unroll 1
         for (int dzi = 0; dzi < NZ; ++dzi) {
-          if (!C::kAllOperands) load_operands(dzi, 0);
-          const int k = C::kAllOperands ? dzi : 0;
-          (void)k;
+          if (!kAll) load_operands(dzi, 0);
           const float* pl = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + kHaloX + lane - C::RX;
           // the weights of this dz plane
           float Wd[NWT];
@@ -191,8 +208,8 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           for (int j = 0; j < 4; ++j) acc[i][j] = accC[i][j] = 0.f;
 #pragma unroll
         for (int dzi = 0; dzi < NZ; ++dzi) {
-          if (!C::kAllOperands) load_operands(dzi, 0);
-          const int k = C::kAllOperands ? dzi : 0;
+          if (!kAll) load_operands(dzi, 0);
+          const int k = kAll ? dzi : 0;
           const float* row0 = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + coff;
           const bool centre_only = STAR && dzi != C::RZ;  // see plane_sp_tf32_centre
           if (MODE == Mode::SpTF32) {
@@ -201,6 +218,9 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           } else if (MODE == Mode::DenseTF32) {
             if (centre_only) plane_dense_tf32_centre<C, C::SX, RIN>(row0, Ad[k], acc);
             else plane_dense_tf32<C, C::SX, RIN>(row0, Ad[k], acc);
+          } else if (centre_only) {
+            plane_split<C, MODE, C::SX, C::RY, C::RY + 1>(args, dzi, lane, row0, Am[k], Em[k], A[k], E[k], acc,
+                                                          accC);
           } else {
             plane_split<C, MODE>(args, dzi, lane, row0, Am[k], Em[k], A[k], E[k], acc, accC);
           }

@@ -384,20 +384,23 @@ def test_chained_calls_equal_one_multistep_call(engine, shape, r, T):
     assert np.any(multi.view(np.uint32) & 0x1FFF)
 
 
-@pytest.mark.parametrize("engine", ["sparse_tc", "dense_tc"])
+@pytest.mark.parametrize("key", [("sparse_tc", "tf32"), ("dense_tc", "tf32"), ("sparse_tc", "f16x2"),
+                                 ("sparse_tc", "bf16x3")])
 @pytest.mark.parametrize("r", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(18, 40, 72), (13, 35, 70)])
-def test_star_3d_skips_zero_operands(engine, r, shape):
+def test_star_3d_skips_zero_operands(key, r, shape):
     # A 3-D star plan skips the A operands of its off-centre planes that hold
-    # only zero coefficients; a box plan with the same coefficients still
-    # issues them.  Adding exact zeros changes nothing: equal results.
+    # only zero coefficients (the split precisions: the cross products of
+    # those rows); a box plan with the same coefficients still issues them.
+    # Adding exact zeros changes nothing: equal results.
+    engine, prec = key
     g = si.rng(14, r)
     u0 = si.grid(shape, -1, 1, g)
     w = si.normalised_coeffs(3, r, "star", g)
-    star = gpu_run(u0, w, 3, "star", "tf32", engine)
-    box = gpu_run(u0, w, 3, "box", "tf32", engine)
-    assert np.array_equal(star, box), (engine, r, shape)
-    check_close(star, oracle.stencil(u0, w, 3), (engine, "tf32"))
+    star = gpu_run(u0, w, 3, "star", prec, engine)
+    box = gpu_run(u0, w, 3, "box", prec, engine)
+    assert np.array_equal(star, box), (key, r, shape)
+    check_close(star, oracle.stencil(u0, w, 3), key)
 
 
 @pytest.mark.parametrize("shape_kind", ["star", "box"])
@@ -607,6 +610,32 @@ def test_batch_routes_match_individual_runs(fuse_min_points, queue_steps):
         spider.batch_configure(0, 0)
     for k in range(len(jobs)):
         assert np.array_equal(outs[k].cpu().numpy(), refs[k]), k
+    for p in plans:
+        p.close()
+
+
+def test_batch_replay_follows_changed_step_counts():
+    # the same plans and buffers with other step counts rebuild the queue;
+    # the same step counts again replay the kept launch: every call gives
+    # the plans' own results
+    jobs = _batch_jobs()[1:8]
+    plans, ins, outs = [], [], []
+    for u0, w, kind, steps in jobs:
+        plans.append(spider.Plan(w, u0.shape, kind, "tf32"))
+        ins.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.empty_like(ins[-1]))
+    counts_a = [j[3] for j in jobs]
+    counts_b = [n + 3 for n in counts_a]
+    refs = {}
+    for name, counts in (("a", counts_a), ("b", counts_b)):
+        refs[name] = [gpu_run(u0, w, n, kind, "tf32") for (u0, w, kind, _), n in zip(jobs, counts)]
+    for name, counts in (("a", counts_a), ("a", counts_a), ("b", counts_b), ("a", counts_a), ("b", counts_b)):
+        for o in outs:
+            o.fill_(float("nan"))
+        spider.batch(plans, ins, outs, counts)
+        torch.cuda.synchronize()
+        for k in range(len(jobs)):
+            assert np.array_equal(outs[k].cpu().numpy(), refs[name][k]), (name, k)
     for p in plans:
         p.close()
 
