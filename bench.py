@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--workload", default="box2d",
                     choices=sorted(WORKLOADS) + ["batched", "batched_small", "serving", "sweep", "mma_peak"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "f16x2", "bf16x3"])
-    ap.add_argument("--engine", default="sparse_tc", choices=["sparse_tc", "dense_tc", "cuda_core", "sparse_tc_copy"])
+    ap.add_argument("--engine", default="sparse_tc",
+                    choices=["sparse_tc", "dense_tc", "cuda_core", "sparse_tc_copy", "sparse_tc_no_co"])
     ap.add_argument("--steps-per-pass", type=int, default=None,
                     help="time steps fused per HBM pass (default: chosen by spider_plan_autotune)")
     ap.add_argument("--tile-variant", type=int, default=None)
@@ -445,25 +446,35 @@ def run_spider(a):
     # comparators and other precisions on the same GPU and workload
     if rank == 0 and not a.no_comparators:
         comps = {}
-        variants = [("sparse_tc", "tf32"), ("sparse_tc", "f16x2"), ("sparse_tc", "bf16x3"), ("dense_tc", "tf32"),
-                    ("cuda_core", "tf32"), ("sparse_tc_copy", "tf32")]
-        for eng, prec in variants:
-            if (eng, prec) == (a.engine, a.precision):
+        # each comparator at its own autotuned setting; the "/T1" entries run
+        # the one-step tile (one step per pass, tile variant 0), the kernel
+        # the explicit-copy and no-CO comparators are built on: dense TC ->
+        # sparse TC without the Sec. 3.3 optimisations -> SPIDER is the
+        # Sec. 4.4 ablation at one step per pass
+        variants = [("sparse_tc", "tf32", None), ("sparse_tc", "f16x2", None), ("sparse_tc", "bf16x3", None),
+                    ("dense_tc", "tf32", None), ("cuda_core", "tf32", None), ("sparse_tc_copy", "tf32", None),
+                    ("sparse_tc_no_co", "tf32", None), ("sparse_tc", "tf32", (1, 0)), ("dense_tc", "tf32", (1, 0))]
+        for eng, prec, fixed in variants:
+            if (eng, prec) == (a.engine, a.precision) and fixed is None:
                 continue
+            name = f"{eng}/{prec}" + ("/T1" if fixed else "")
             try:
                 p2 = spider.Plan(w, wl.extents, wl.shape, prec, eng)
             except spider.SpiderError as err:  # e.g. radius 4..7 exists for sparse TF32 only
-                comps[f"{eng}/{prec}"] = {"value": None, "unsupported": str(err)}
+                comps[name] = {"value": None, "unsupported": str(err)}
                 continue
-            t2, v2 = p2.autotune(a_in, b_out, wl.steps, stream)   # each comparator at its own best setting
+            if fixed:
+                t2, v2 = fixed
+                p2.set_tile_variant(v2)
+            else:
+                t2, v2 = p2.autotune(a_in, b_out, wl.steps, stream)
             iters = max(3, a.steps // 10)
             for _ in range(2):
                 p2.run(a_in, b_out, wl.steps, stream)
             torch.cuda.synchronize(dev)
             d2 = time_runs(p2, a_in, b_out, wl.steps, iters, flush, stream)
             p2.sync(stream)
-            comps[f"{eng}/{prec}"] = {"value": pts * wl.steps * iters / d2 / 1e9, "steps_per_pass": t2,
-                                      "tile_variant": v2}
+            comps[name] = {"value": pts * wl.steps * iters / d2 / 1e9, "steps_per_pass": t2, "tile_variant": v2}
             p2.close()
         result["comparators"] = comps
 

@@ -78,12 +78,18 @@ typedef enum { SPIDER_TF32 = 0, SPIDER_F16X2 = 1, SPIDER_BF16X3 = 2, SPIDER_AUTO
  * sets its own design against: an explicit copy of every input window, in
  * the swapped order, into a shared-memory buffer of its own, which the MMA
  * operands then load contiguously (2-D, TF32, radius 1..3, one step per
- * pass; the same products as SPARSE_TC, bit for bit). */
+ * pass; the same products as SPARSE_TC, bit for bit).  SPARSE_TC_NO_CO is
+ * SPIDER without the computing optimisations of Sec. 3.3 (the "SpTC" step
+ * of the Sec. 4.4 ablation): the packed kernel matrix and metadata are
+ * staged in shared memory and every MMA loads its A operand and metadata
+ * from there, instead of keeping them in registers for the whole kernel
+ * (2-D, TF32, radius 1..3, one step per pass; bit for bit SPARSE_TC's). */
 typedef enum {
   SPIDER_ENGINE_SPARSE_TC = 0,
   SPIDER_ENGINE_DENSE_TC = 1,
   SPIDER_ENGINE_CUDA_CORE = 2,
-  SPIDER_ENGINE_SPARSE_TC_COPY = 3
+  SPIDER_ENGINE_SPARSE_TC_COPY = 3,
+  SPIDER_ENGINE_SPARSE_TC_NO_CO = 4
 } spider_engine;
 
 /* spider_plan_create -- the paper's offline transform (Sec. 3.1, Sec. 3.3.2).
@@ -115,9 +121,10 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
                                  const float* coeffs, spider_precision prec, spider_plan* out);
 
 /* Selects the kernel the plan runs (default SPIDER_ENGINE_SPARSE_TC).  The
- * comparators support SPIDER_TF32 (DENSE_TC, SPARSE_TC_COPY) and plain FP32
- * (CUDA_CORE, precision ignored), radius 1..3; SPARSE_TC_COPY 2-D grids only
- * (SPIDER_ERR_UNSUPPORTED otherwise). */
+ * comparators support SPIDER_TF32 (DENSE_TC, SPARSE_TC_COPY, SPARSE_TC_NO_CO)
+ * and plain FP32 (CUDA_CORE, precision ignored), radius 1..3;
+ * SPARSE_TC_COPY and SPARSE_TC_NO_CO 2-D grids only (SPIDER_ERR_UNSUPPORTED
+ * otherwise). */
 spider_status spider_plan_set_engine(spider_plan plan, spider_engine engine);
 
 /* Time steps fused per pass over HBM (1 = one launch per step).  Built: 1..4

@@ -13,11 +13,12 @@ import numpy as np
 
 from . import _native
 from ._native import (SPIDER_BF16X3, SPIDER_BOX, SPIDER_ENGINE_CUDA_CORE, SPIDER_ENGINE_DENSE_TC,
-                      SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_SPARSE_TC_COPY, SPIDER_F16X2, SPIDER_STAR, SPIDER_TF32, SpiderError, check)
+                      SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_SPARSE_TC_COPY, SPIDER_ENGINE_SPARSE_TC_NO_CO, SPIDER_F16X2, SPIDER_STAR, SPIDER_TF32, SpiderError, check)
 
 PRECISIONS = {"tf32": SPIDER_TF32, "f16x2": SPIDER_F16X2, "bf16x3": SPIDER_BF16X3}
 ENGINES = {"sparse_tc": SPIDER_ENGINE_SPARSE_TC, "dense_tc": SPIDER_ENGINE_DENSE_TC,
-           "cuda_core": SPIDER_ENGINE_CUDA_CORE, "sparse_tc_copy": SPIDER_ENGINE_SPARSE_TC_COPY}
+           "cuda_core": SPIDER_ENGINE_CUDA_CORE, "sparse_tc_copy": SPIDER_ENGINE_SPARSE_TC_COPY,
+           "sparse_tc_no_co": SPIDER_ENGINE_SPARSE_TC_NO_CO}
 SHAPES = {"star": SPIDER_STAR, "box": SPIDER_BOX}
 
 

@@ -26,6 +26,7 @@ SPIDER_STAR, SPIDER_BOX = 0, 1
 SPIDER_TF32, SPIDER_F16X2, SPIDER_BF16X3, SPIDER_AUTO = 0, 1, 2, 3
 # spider_engine
 SPIDER_ENGINE_SPARSE_TC, SPIDER_ENGINE_DENSE_TC, SPIDER_ENGINE_CUDA_CORE, SPIDER_ENGINE_SPARSE_TC_COPY = 0, 1, 2, 3
+SPIDER_ENGINE_SPARSE_TC_NO_CO = 4
 
 # name -> (restype, argtypes); the complete list of entry points of spider.h
 SIGNATURES = {

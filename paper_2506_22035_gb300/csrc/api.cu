@@ -168,7 +168,7 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
 
 // Enqueues `steps` steps from `in` to `out` (device pointers) on `stream`.
 int max_steps_per_pass(const spider_plan_t* p) {
-  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY) return 1;
+  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY || p->engine == SPIDER_ENGINE_SPARSE_TC_NO_CO) return 1;
   if (p->wide()) return p->ndim == 1 ? 4 : 1;
   const bool sparse_tf32 = p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3;
   if (p->ndim == 2) return sparse_tf32 ? max_deep_steps(p->r) : 4;  // deep tiles beyond 4
@@ -204,7 +204,8 @@ ErrorModel error_model(const spider_plan_t* p, spider_precision prec, spider_eng
     m.floor = 3e-7;
     return m;
   }
-  if (engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY) {
+  if (engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
+      engine == SPIDER_ENGINE_SPARSE_TC_NO_CO) {
     m.built = p->r <= kMaxR && prec == SPIDER_TF32 && (engine == SPIDER_ENGINE_DENSE_TC || p->ndim == 2);
     m.wsum = p->wsum_rel[0];
     m.drift = 1e-4;
@@ -293,6 +294,7 @@ spider_status run_device(spider_plan_t* p, const float* in, float* out, int64_t 
   // the next pass would round it, and that pass skips the rounding; the
   // caller's input is rounded on load and the final grid is stored unrounded.
   const bool tf32 = p->engine == SPIDER_ENGINE_DENSE_TC || p->engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
+                    p->engine == SPIDER_ENGINE_SPARSE_TC_NO_CO ||
                     (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3);
   float* bufs[2] = {out, p->dev.scratch};
   int first = (npasses % 2 == 1) ? 0 : 1;  // packed: the last pass lands in out
@@ -460,12 +462,14 @@ spider_status spider_plan_create(int ndim, const int64_t* extents, spider_shape 
 
 spider_status spider_plan_set_engine(spider_plan p, spider_engine engine) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
-  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_COPY)
+  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_NO_CO)
     return fail(SPIDER_ERR_INVALID, "bad engine");
-  if ((engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY) && p->prec != SPIDER_TF32)
-    return fail(SPIDER_ERR_UNSUPPORTED, "the dense and explicit-copy comparators run TF32 only");
-  if (engine == SPIDER_ENGINE_SPARSE_TC_COPY && p->ndim != 2)
-    return fail(SPIDER_ERR_UNSUPPORTED, "the explicit-copy comparator is built for 2-D grids");
+  const bool tf32_only = engine == SPIDER_ENGINE_DENSE_TC || engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
+                         engine == SPIDER_ENGINE_SPARSE_TC_NO_CO;
+  if (tf32_only && p->prec != SPIDER_TF32)
+    return fail(SPIDER_ERR_UNSUPPORTED, "the dense, explicit-copy and no-CO comparators run TF32 only");
+  if ((engine == SPIDER_ENGINE_SPARSE_TC_COPY || engine == SPIDER_ENGINE_SPARSE_TC_NO_CO) && p->ndim != 2)
+    return fail(SPIDER_ERR_UNSUPPORTED, "the explicit-copy and no-CO comparators are built for 2-D grids");
   if (engine != SPIDER_ENGINE_SPARSE_TC && p->r > kMaxR)
     return fail(SPIDER_ERR_UNSUPPORTED, "radius 4..7 is built for the sparse tensor-core engine only");
   std::lock_guard<std::mutex> lock(p->mu);
@@ -573,7 +577,7 @@ spider_status spider_plan_error_bound(spider_plan p, spider_precision prec, spid
   if (steps < 0) return fail(SPIDER_ERR_INVALID, "steps must be >= 0");
   if (prec == SPIDER_AUTO) prec = SPIDER_TF32;
   if (prec < SPIDER_TF32 || prec > SPIDER_BF16X3) return fail(SPIDER_ERR_INVALID, "bad precision");
-  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_COPY)
+  if (engine < SPIDER_ENGINE_SPARSE_TC || engine > SPIDER_ENGINE_SPARSE_TC_NO_CO)
     return fail(SPIDER_ERR_INVALID, "bad engine");
   const ErrorModel m = error_model(p, prec, engine);
   if (!m.built) return fail(SPIDER_ERR_UNSUPPORTED, "no kernel for this stencil in that arithmetic");

@@ -75,6 +75,7 @@ cudaError_t launch_step(const LaunchCtx& ctx) {
     case SPIDER_ENGINE_CUDA_CORE: return launch_cuda_core(cls, p->r, ctx);
     case SPIDER_ENGINE_DENSE_TC: return launch_dense_tf32(cls, p->r, ctx);
     case SPIDER_ENGINE_SPARSE_TC_COPY: return launch_sp_tf32_copy(cls, p->r, ctx);
+    case SPIDER_ENGINE_SPARSE_TC_NO_CO: return launch_sp_tf32_no_co(cls, p->r, ctx);
     default: break;
   }
   switch (p->prec) {
@@ -91,7 +92,8 @@ namespace spider {
 cudaError_t launch_pass(const LaunchCtx& ctx, int T) {
   if (T <= 1) return launch_step(ctx);
   const spider_plan_t* p = ctx.plan;
-  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY) return cudaErrorNotSupported;
+  if (p->engine == SPIDER_ENGINE_SPARSE_TC_COPY || p->engine == SPIDER_ENGINE_SPARSE_TC_NO_CO)
+    return cudaErrorNotSupported;
   if (p->ndim == 1) return p->wide() ? launch_wide1d_fused_sp_tf32(p->r, T, ctx) : cudaErrorNotSupported;
   if (p->ndim == 3) {
     if (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 && p->prec != SPIDER_BF16X3)

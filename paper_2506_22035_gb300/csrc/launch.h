@@ -39,6 +39,8 @@ cudaError_t launch_dense_tf32(int cls, int r, const LaunchCtx& ctx);
 cudaError_t launch_cuda_core(int cls, int r, const LaunchCtx& ctx);
 // SPIDER_ENGINE_SPARSE_TC_COPY: the explicit row-swap copy (2-D only).
 cudaError_t launch_sp_tf32_copy(int cls, int r, const LaunchCtx& ctx);
+// SPIDER_ENGINE_SPARSE_TC_NO_CO: operands from shared memory per MMA (2-D only).
+cudaError_t launch_sp_tf32_no_co(int cls, int r, const LaunchCtx& ctx);
 // Radius 4..7 (1-D and 2-D), sparse TF32, wide layout.
 cudaError_t launch_wide_sp_tf32(int cls, int r, const LaunchCtx& ctx);
 // Fused passes of T = 2..4 steps for 1-D sparse TF32 plans (wide layout,

@@ -153,6 +153,7 @@ extern "C" spider_status spider_run_static(spider_plan p, const float* grid_in, 
   const int rem = (int)(body % T);
   const int64_t npasses = head + full + (rem ? 1 : 0);
   const bool tf32 = tma_out && (p->engine == SPIDER_ENGINE_DENSE_TC || p->engine == SPIDER_ENGINE_SPARSE_TC_COPY ||
+                                p->engine == SPIDER_ENGINE_SPARSE_TC_NO_CO ||
                                 (p->engine == SPIDER_ENGINE_SPARSE_TC && p->prec != SPIDER_F16X2 &&
                                  p->prec != SPIDER_BF16X3));
   LaunchCtx ctx;

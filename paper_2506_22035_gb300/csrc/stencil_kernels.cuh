@@ -34,7 +34,18 @@ namespace spider {
 
 // SpTF32Copy: SpTF32 with the input row swap done by an explicit copy of
 // every window into a buffer of its own (the baseline of Sec. 3.2).
-enum class Mode : int { SpTF32 = 0, SpF16x2 = 1, SpBF16x3 = 2, DenseTF32 = 3, CudaCore = 4, SpTF32Copy = 5 };
+// SpTF32NoCO: SpTF32 without the computing optimisations of Sec. 3.3: the
+// kernel-matrix operands and metadata are staged in shared memory and every
+// MMA loads its own from there instead of keeping them in registers.
+enum class Mode : int {
+  SpTF32 = 0,
+  SpF16x2 = 1,
+  SpBF16x3 = 2,
+  DenseTF32 = 3,
+  CudaCore = 4,
+  SpTF32Copy = 5,
+  SpTF32NoCO = 6
+};
 
 struct StepArgs {
   const float* src;        // source grid (generic loader only)
@@ -59,16 +70,21 @@ struct StepArgs {
 // load (each input value is loaded about 2.75 times by overlapping windows
 // and warp tiles).
 __host__ __device__ constexpr bool is_tf32_mode(Mode m) {
-  return m == Mode::SpTF32 || m == Mode::DenseTF32 || m == Mode::SpTF32Copy;
+  return m == Mode::SpTF32 || m == Mode::DenseTF32 || m == Mode::SpTF32Copy || m == Mode::SpTF32NoCO;
 }
-__host__ __device__ constexpr bool is_sp_tf32(Mode m) { return m == Mode::SpTF32 || m == Mode::SpTF32Copy; }
+__host__ __device__ constexpr bool is_sp_tf32(Mode m) {
+  return m == Mode::SpTF32 || m == Mode::SpTF32Copy || m == Mode::SpTF32NoCO;
+}
 
 // Shared memory of the one-step kernel: two input stages, barriers and, for
 // SpTF32Copy, the buffer of swapped windows (every row's BX / 8 windows of 16
-// points, twice the row: consecutive windows overlap by 8 points).
+// points, twice the row: consecutive windows overlap by 8 points); for
+// SpTF32NoCO, the packed operands and metadata of every A index of a plane.
 template <class C, Mode MODE>
 __host__ __device__ constexpr int step_window_bytes() {
-  return MODE == Mode::SpTF32Copy ? C::SY * C::SZ * (C::BX / 8) * 16 * 4 : 0;
+  return MODE == Mode::SpTF32Copy   ? C::SY * C::SZ * (C::BX / 8) * 16 * 4
+         : MODE == Mode::SpTF32NoCO ? C::NA * 32 * (16 + 4)
+                                    : 0;
 }
 template <class C, Mode MODE>
 __host__ __device__ constexpr int step_smem_bytes() {
@@ -127,6 +143,33 @@ template <class C, int SP = C::SX, bool ROUND = true, int AMIN = 0, int AMAX = C
 __device__ __forceinline__ void plane_sp_tf32(const float* row0, const uint4 (&A)[C::NA],
                                               const uint32_t (&E)[C::NA], float (&acc)[C::H / 2][4]) {
   sp_tf32_row<C, SP, ROUND, AMIN, AMIN, AMAX>(smem_u32(row0), A, E, acc);
+}
+
+// SpTF32NoCO: as sp_tf32_row, with every MMA's A operand and metadata read
+// from shared memory: this lane's uint4 of A index a at ops_a + 512 a, its
+// metadata word at ops_e + 128 a (the packed layout, 32 lanes per index).
+// The loads are volatile, so the compiler cannot keep the operands in
+// registers across tiles.
+template <class C, int SP, bool ROUND, int JJ>
+__device__ __forceinline__ void sp_tf32_row_smem_ops(uint32_t addr, uint32_t ops_a, uint32_t ops_e,
+                                                     float (&acc)[C::H / 2][4]) {
+  const float4 v = lds128_at<JJ * SP * 4>(addr);
+  const uint32_t b[4] = {ROUND ? cvt_tf32(v.x) : __float_as_uint(v.x), ROUND ? cvt_tf32(v.y) : __float_as_uint(v.y),
+                         ROUND ? cvt_tf32(v.z) : __float_as_uint(v.z), ROUND ? cvt_tf32(v.w) : __float_as_uint(v.w)};
+#pragma unroll
+  for (int pp = 0; pp < C::H / 2; ++pp) {
+    const int a = JJ - 2 * pp;
+    if (a >= 0 && a < C::NA) {
+      uint4 av;
+      uint32_t e;
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(av.x), "=r"(av.y), "=r"(av.z), "=r"(av.w)
+                   : "r"(ops_a + (uint32_t)(a * 32 * 16)));
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(ops_e + (uint32_t)(a * 32 * 4)));
+      mma_sp_tf32(acc[pp], av, e, b);
+    }
+  }
+  if constexpr (JJ + 1 <= C::H - 2 + C::NA - 1) sp_tf32_row_smem_ops<C, SP, ROUND, JJ + 1>(addr, ops_a, ops_e, acc);
 }
 
 template <class C, int SP, bool ROUND, int JJ, int AMIN, int AMAX>
@@ -385,7 +428,9 @@ __global__ void __launch_bounds__(C::kThreads)
   uint32_t Em[C::RY + 1];
   float W[(2 * C::RY + 1) * (2 * C::RX + 1)];
   auto load_operands = [&](int dzi) {
-    if (is_sp_tf32(MODE)) {
+    if (MODE == Mode::SpTF32NoCO) {
+      // staged in shared memory below and read there by every MMA
+    } else if (is_sp_tf32(MODE)) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         if (STAR && dzi != C::RZ && a != C::RY && a != C::RY + 1) continue;  // zero operands
@@ -410,6 +455,19 @@ __global__ void __launch_bounds__(C::kThreads)
     }
   };
   if (C::RZ == 0) load_operands(0);
+  // SpTF32NoCO (2-D): the plane's packed operands, then its metadata words
+  const uint32_t ops_smem = smem_u32(smem + 2 * C::kStageStride + 64);
+  if constexpr (MODE == Mode::SpTF32NoCO) {
+    static_assert(C::RZ == 0, "2-D only");
+    uint4* oa = reinterpret_cast<uint4*>(smem + 2 * C::kStageStride + 64);
+    uint32_t* oe = reinterpret_cast<uint32_t*>(oa + NA * 32);
+    for (int i = tid; i < NA * 32; i += C::kThreads) {
+      oa[i] = args.a_words[i];
+      oe[i] = args.meta[i];
+    }
+    __syncthreads();
+  }
+  (void)ops_smem;
 
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -507,6 +565,9 @@ __global__ void __launch_bounds__(C::kThreads)
           const float* wrow0 = Wb + (wy * C::H) * WP + (wx * 8 + g) * 16 + 4 * q;
           plane_sp_tf32<C, WP, RIN>(wrow0, A, E, acc);
           __syncthreads();  // the buffer is rewritten for the next plane or tile
+        } else if (MODE == Mode::SpTF32NoCO) {
+          sp_tf32_row_smem_ops<C, C::SX, RIN, 0>(smem_u32(row0), ops_smem + 16u * lane,
+                                                 ops_smem + (uint32_t)(NA * 32 * 16) + 4u * lane, acc);
         } else if (MODE == Mode::SpTF32) {
           if (centre_only) plane_sp_tf32_centre<C, C::SX, RIN>(row0, A, E, acc);
           else plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);

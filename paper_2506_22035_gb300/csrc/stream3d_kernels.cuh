@@ -58,10 +58,12 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
   constexpr int CPP = MODE == Mode::SpF16x2 ? (C::RY + 1) + NA : NA;
   constexpr int NZ = 2 * C::RZ + 1;
   constexpr int NWT = (2 * C::RY + 1) * (2 * C::RX + 1);
-  // operands: all dz planes (small TF32 stencils) or one plane at a time;
-  // the FP16 split keeps one plane's (its 32 accumulators leave no room for
-  // three planes' operands at two or more CTAs per SM)
-  constexpr bool kAll = C::kAllOperands && MODE != Mode::SpF16x2;
+  // operands: all dz planes (small stencils) or one plane at a time.  The
+  // FP16 split of a star keeps one plane's (143 instead of 244 registers,
+  // three CTAs per SM instead of two: Heat-3D 447 against 428 GStencil/s);
+  // for a box, loading the larger operand sets plane by plane costs more than
+  // the third CTA gains (Box-3D 377 against 408)
+  constexpr bool kAll = C::kAllOperands && !(MODE == Mode::SpF16x2 && STAR);
   constexpr int NPL = kAll ? NZ : 1;
   uint4 A[NPL][NA];
   uint32_t E[NPL][NA];

@@ -616,3 +616,23 @@ def test_batched_workload_generators_match_their_descriptions():
     assert all(256 <= s <= 4096 for j in mix for s in j.extents)
     assert all(10 <= j.steps <= 200 and 1 <= j.r <= 3 for j in small + mix)
     assert si.batched_small_jobs() == small and si.batched_jobs() == mix
+
+
+@pytest.mark.parametrize("engine", ["sparse_tc_copy", "sparse_tc_no_co"])
+def test_one_step_comparator_engines_are_2d_tf32_only(lib, engine):
+    # host-side checks (no device work): the explicit-copy and no-CO
+    # comparators exist for 2-D TF32 plans of radius 1..3, one step per pass
+    import stencil_inputs as si
+    w2 = si.normalised_coeffs(2, 2, "box", si.rng(31, 0))
+    p = spider.Plan(w2, (40, 72), "box", "tf32", engine)
+    with pytest.raises(spider.SpiderError) as e:
+        p.set_steps_per_pass(2)
+    assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
+    assert p.error_bound(100, "tf32", engine) == pytest.approx(p.error_bound(100, "tf32", "dense_tc"))
+    p.close()
+    for ext, prec in (((40, 72), "f16x2"), ((40, 72), "bf16x3"), ((8, 16, 72), "tf32")):
+        p = spider.Plan(si.normalised_coeffs(len(ext), 1, "box", si.rng(31, 1)), ext, "box", prec)
+        with pytest.raises(spider.SpiderError) as e:
+            p.set_engine(engine)
+        assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
+        p.close()

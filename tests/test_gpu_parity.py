@@ -339,6 +339,42 @@ def test_explicit_swap_copy_engine_limits():
     p2.close()
 
 
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(130, 260), (67, 133), (64, 64)])
+def test_no_co_engine_equals_the_register_resident_operands(r, shape):
+    # SPARSE_TC_NO_CO reads every MMA's A operand and metadata from shared
+    # memory instead of registers: the same products in the same order, so
+    # results are bit-identical to SPARSE_TC on the one-step tile, and
+    # integer inputs exact
+    g = si.rng(29, r)
+    u0 = si.grid(shape, -1, 1, g)
+    w = si.normalised_coeffs(2, r, "box", g)
+    no_co = gpu_run(u0, w, 3, "box", "tf32", "sparse_tc_no_co")
+    ref = gpu_run(u0, w, 3, "box", "tf32", "sparse_tc")
+    assert np.array_equal(no_co, ref)
+    check_close(no_co, oracle.stencil(u0, w, 3), ("sparse_tc", "tf32"))
+    ui, wi = int_case(shape, r, seed=r + 50)
+    assert np.array_equal(gpu_run(ui, wi, 2, "box", "tf32", "sparse_tc_no_co").astype(np.float64),
+                          oracle.stencil(ui, wi, 2))
+
+
+def test_no_co_engine_limits():
+    w2 = si.normalised_coeffs(2, 1, "box", si.rng(30, 0))
+    p = spider.Plan(w2, (64, 64), "box", "f16x2")
+    with pytest.raises(spider.SpiderError):
+        p.set_engine("sparse_tc_no_co")         # TF32 only
+    p.close()
+    w3 = si.normalised_coeffs(3, 1, "box", si.rng(30, 1))
+    p3 = spider.Plan(w3, (8, 16, 64), "box", "tf32")
+    with pytest.raises(spider.SpiderError):
+        p3.set_engine("sparse_tc_no_co")        # 2-D only
+    p3.close()
+    p2 = spider.Plan(w2, (64, 64), "box", "tf32", "sparse_tc_no_co")
+    with pytest.raises(spider.SpiderError):
+        p2.set_steps_per_pass(2)                # one step per pass
+    p2.close()
+
+
 @pytest.mark.parametrize("shape,offset", [((301, 517), 0), ((200, 324), 1), ((64, 132), 0)])
 def test_vector_store_variant_on_ragged_and_unaligned_grids(shape, offset):
     # variant 5 writes the last level with 16-byte stores only where rows
