@@ -54,13 +54,12 @@ static_assert(2 * (kSmemBase + kMaxTableSmem + 1024) <= 228 * 1024, "two CTAs pe
 // Grids of at least this many points (with more than one step) run as fused
 // passes of their own on side streams; smaller ones, and single steps, go
 // through the persistent queue.  Measured on the mixed batch of 64 grids of
-// 256^2..4096^2 (GStencil/s, replayed): threshold 2^21: 867, 2^19: 1000,
-// 2^18: 1014, 2^16 (every grid of the mix fused): 1114 -- a queue item
-// carries one step and each step of a job waits for the previous one, so a
-// small job with many steps is a chain of queue latencies, where its fused
-// passes replayed as a graph take two steps per few-microsecond launch.
-// Below it the queue wins: 256 grids of 32^2..255^2 points run at 188
-// GStencil/s through it and at 41 as fused passes on side streams.
+// 256^2..4096^2 (GStencil/s, replayed), with two fused steps per queue item:
+// threshold 2^20: 1026, 2^18: 1066, 2^17: 1045, 2^16 (every grid of the mix
+// fused): 1118, every grid in the queue: 883 -- the side streams run each
+// grid with its own tuned tile and depth.  Below it the queue wins: 256 grids
+// of 32^2..255^2 points run at 244 GStencil/s through it and at 41 as fused
+// passes on side streams (grids of a few tiles are all launch latency).
 constexpr long long kFuseMinPoints = 1LL << 16;
 constexpr int kQueueStepsPerItem = 2;
 // Routing of spider_batch (spider_batch_configure): grids of at least
