@@ -110,9 +110,11 @@ size_t job_bytes(const spider_plan_t* p) {
 // Measured speed of the arithmetics per stencil class (GStencil/s on one
 // GB300, autotuned, 2048^2 2-D and 160^3 3-D grids of U[0,1) values), used
 // to rank the arithmetics whose error bound meets a job's target, and the
-// steps per pass / tile variant the autotuner chose there.  FP32 on CUDA
-// cores beats the FP16 split for radius 1 and 3-D radius 2; the split wins
-// for larger 2-D stencils and 3-D radius 3.
+// steps per pass / tile variant the autotuner chose there.  2-D: FP32 on
+// CUDA cores beats the FP16 split for radius 1, the split wins for larger
+// stencils.  3-D (by shape: a star's off-centre planes hold one weight):
+// CUDA cores beat the split for every star and the radius-1 box, the split
+// wins for the radius-2 and radius-3 boxes.
 struct ClassRate {
   double tf32, f16x2, cuda_core;
   int t_tf32, v_tf32, t_f16, v_f16, t_cc, v_cc;
@@ -120,10 +122,13 @@ struct ClassRate {
 ClassRate class_rate(const spider_plan_t* p) {
   const int r = std::min(p->r, kMaxR);
   if (p->ndim == 3) {
-    static const ClassRate k3[3] = {{245, 140, 165, 1, 0, 1, 0, 1, 0},
-                                    {165, 64, 76, 1, 0, 1, 0, 1, 0},
-                                    {117, 35, 30, 1, 0, 1, 0, 1, 0}};
-    return k3[r - 1];
+    static const ClassRate star[3] = {{242, 139, 219, 1, 0, 1, 0, 1, 0},
+                                      {192, 131, 191, 1, 0, 1, 0, 1, 0},
+                                      {147, 88, 158, 1, 0, 1, 0, 1, 0}};
+    static const ClassRate box[3] = {{229, 137, 162, 1, 0, 1, 0, 1, 0},
+                                     {136, 83, 79, 1, 0, 1, 0, 1, 0},
+                                     {85, 42, 32, 1, 0, 1, 0, 1, 0}};
+    return p->shape == SPIDER_STAR ? star[r - 1] : box[r - 1];
   }
   static const ClassRate k2[3] = {{998, 636, 731, 3, 3, 2, 4, 2, 4},
                                   {809, 494, 477, 2, 3, 2, 3, 1, 0},

@@ -1,6 +1,8 @@
 // Template launcher shared by the per-mode dispatch translation units.
 #pragma once
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -201,22 +203,34 @@ cudaError_t launch_stream3d(const LaunchCtx& ctx) {
 
 // Tile shapes per stencil class: 1-D, 2-D (64 x 128 outputs, 8 warps),
 // 3-D (z-streaming 32 x 128 column blocks; cube tiles of planes x 16 x 128
-// outputs when the grid's rows are not TMA-describable).
+// outputs when the grid's rows are not TMA-describable).  The 3-D column
+// block of radius 1 is 4 warps of 16 rows (its ring of 4 planes leaves room
+// for two to three CTAs per SM).  Radius 2 and 3 keep 6 and 8 planes in
+// flight, one CTA per SM, and there 8 warps of 8 rows run faster (GStencil/s
+// at 160^3 / 320^3, 4 -> 8 warps: FP16 split radius-3 box 35 -> 42 / 46 ->
+// 56, star 57 -> 88 / 79 -> 124; CUDA cores radius-3 star 131 -> 158 / 201
+// -> 248), except for TF32 at radius 3, whose 16-row warp tiles feed more
+// MMAs per row load (box 85 / 115 with 4 warps against 63 / 81 with 8).
+template <int R, Mode MODE>
+using Stream3DCfg = typename std::conditional<R >= 2 && !(R == 3 && is_tf32_mode(MODE)), StreamCfg<R, 4, 2, 8, 0>,
+                                              StreamCfg<R, 2, 2, 16, 0>>::type;
+
 template <int R, Mode MODE>
 cudaError_t launch_class(int cls, const LaunchCtx& ctx) {
   if (cls == 1) return launch_cfg<TileCfg<0, 0, R, 1, 1, 2, 2>, MODE>(ctx);
   if (cls == 2) return launch_cfg<TileCfg<0, R, R, 1, 4, 2, 16>, MODE>(ctx);
   if (cls == 3) {
-    // star stencils skip the zero operands of the off-centre planes (the
-    // cube tiles, for grids TMA cannot read, in TF32 only)
-    if constexpr (MODE != Mode::CudaCore) {
+    // star stencils skip the zero operands (CUDA cores: the zero weights)
+    // of the off-centre planes (the cube tiles, for grids TMA cannot read,
+    // in TF32 only)
+    {
       if (ctx.plan->shape == SPIDER_STAR) {
-        const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE, true>(ctx);
+        const cudaError_t e = launch_stream3d<Stream3DCfg<R, MODE>, MODE, true>(ctx);
         if (e != cudaErrorNotSupported) return e;
         if constexpr (is_tf32_mode(MODE)) return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE, true>(ctx);
       }
     }
-    const cudaError_t e = launch_stream3d<StreamCfg<R, 2, 2, 16, 0>, MODE>(ctx);
+    const cudaError_t e = launch_stream3d<Stream3DCfg<R, MODE>, MODE>(ctx);
     if (e != cudaErrorNotSupported) return e;
     return launch_cfg<TileCfg<R, R, R, (R <= 2 ? 4 : 2), 1, 2, 16>, MODE>(ctx);
   }

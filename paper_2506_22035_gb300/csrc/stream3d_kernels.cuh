@@ -165,15 +165,31 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
         for (int dzi = 0; dzi < NZ; ++dzi) {
           if (!kAll) load_operands(dzi, 0);
           const float* pl = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + kHaloX + lane - C::RX;
-          // the weights of this dz plane
+          if (STAR && dzi != C::RZ) {
+            // off-centre plane of a star: its one non-zero weight, the
+            // centre; the other products are exact zeros in the box loop
+            // below, so skipping them keeps the result bit for bit
+            const float wv = args.w[(size_t)dzi * NWT + C::RY * (2 * C::RX + 1) + C::RX];
+#pragma unroll
+            for (int yy = 0; yy < C::H; ++yy) {
+              acc[yy][0] = fmaf(wv, pl[(yy + C::RY) * C::SX + C::RX], acc[yy][0]);
+              acc[yy][1] = fmaf(wv, pl[(yy + C::RY) * C::SX + 32 + C::RX], acc[yy][1]);
+            }
+            continue;
+          }
+          // the weights of this dz plane (a star's centre plane: row dy = 0
+          // and column dx = 0 only)
           float Wd[NWT];
 #pragma unroll
           for (int i = 0; i < NWT; ++i) Wd[i] = args.w[(size_t)dzi * NWT + i];
 #pragma unroll
           for (int jj = 0; jj < C::H + 2 * C::RY; ++jj) {
+            // a star reads the whole row only where it is some output's dy = 0 row
+            const bool full_row = !STAR || (jj >= C::RY && jj < C::RY + C::H);
             float in0[2 * C::RX + 1], in1[2 * C::RX + 1];
 #pragma unroll
             for (int kx = 0; kx < 2 * C::RX + 1; ++kx) {
+              if (!full_row && kx != C::RX) continue;
               in0[kx] = pl[jj * C::SX + kx];
               in1[kx] = pl[jj * C::SX + 32 + kx];
             }
@@ -183,6 +199,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
               if (dy >= -C::RY && dy <= C::RY) {
 #pragma unroll
                 for (int kx = 0; kx < 2 * C::RX + 1; ++kx) {
+                  if (STAR && dy != 0 && kx != C::RX) continue;
                   const float wv = Wd[(dy + C::RY) * (2 * C::RX + 1) + kx];
                   acc[yy][0] = fmaf(wv, in0[kx], acc[yy][0]);
                   acc[yy][1] = fmaf(wv, in1[kx], acc[yy][1]);

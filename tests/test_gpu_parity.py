@@ -421,14 +421,15 @@ def test_chained_calls_equal_one_multistep_call(engine, shape, r, T):
 
 
 @pytest.mark.parametrize("key", [("sparse_tc", "tf32"), ("dense_tc", "tf32"), ("sparse_tc", "f16x2"),
-                                 ("sparse_tc", "bf16x3")])
+                                 ("sparse_tc", "bf16x3"), ("cuda_core", "tf32")])
 @pytest.mark.parametrize("r", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(18, 40, 72), (13, 35, 70)])
 def test_star_3d_skips_zero_operands(key, r, shape):
     # A 3-D star plan skips the A operands of its off-centre planes that hold
     # only zero coefficients (the split precisions: the cross products of
-    # those rows); a box plan with the same coefficients still issues them.
-    # Adding exact zeros changes nothing: equal results.
+    # those rows; CUDA cores: the zero weights); a box plan with the same
+    # coefficients still issues them.  Adding exact zeros changes nothing:
+    # equal results.
     engine, prec = key
     g = si.rng(14, r)
     u0 = si.grid(shape, -1, 1, g)
