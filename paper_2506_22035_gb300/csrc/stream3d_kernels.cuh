@@ -158,13 +158,18 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
       const int ybase = y0 + wy * C::H, xbase = x0 + wx * 64;
       const int coff = 8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
       if (MODE == Mode::CudaCore) {
+        // FP32 FMA stencil: lane l computes columns 2l and 2l + 1 of its
+        // warp's 64; per input row it loads the 2r + 2 floats those read as
+        // 8-byte pairs (v[e] = box column 2l + e of the warp, e = 0..9; the
+        // block's column c sits at box column c + 4)
+        constexpr int E0 = (4 - C::RX) / 2, E1 = (5 + C::RX) / 2;  // pairs e = 2m, 2m + 1 for m in [E0, E1]
         float acc[C::H][2];
 #pragma unroll
         for (int i = 0; i < C::H; ++i) acc[i][0] = acc[i][1] = 0.f;
 #pragma unroll 1
         for (int dzi = 0; dzi < NZ; ++dzi) {
           if (!kAll) load_operands(dzi, 0);
-          const float* pl = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + kHaloX + lane - C::RX;
+          const float* pl = slot_ptr(slot_of(z - C::RZ + dzi)) + (wy * C::H) * C::SX + wx * 64 + 2 * lane;
           if (STAR && dzi != C::RZ) {
             // off-centre plane of a star: its one non-zero weight, the
             // centre; the other products are exact zeros in the box loop
@@ -172,8 +177,9 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
             const float wv = args.w[(size_t)dzi * NWT + C::RY * (2 * C::RX + 1) + C::RX];
 #pragma unroll
             for (int yy = 0; yy < C::H; ++yy) {
-              acc[yy][0] = fmaf(wv, pl[(yy + C::RY) * C::SX + C::RX], acc[yy][0]);
-              acc[yy][1] = fmaf(wv, pl[(yy + C::RY) * C::SX + 32 + C::RX], acc[yy][1]);
+              const float2 c = *reinterpret_cast<const float2*>(pl + (yy + C::RY) * C::SX + kHaloX);
+              acc[yy][0] = fmaf(wv, c.x, acc[yy][0]);
+              acc[yy][1] = fmaf(wv, c.y, acc[yy][1]);
             }
             continue;
           }
@@ -186,12 +192,13 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           for (int jj = 0; jj < C::H + 2 * C::RY; ++jj) {
             // a star reads the whole row only where it is some output's dy = 0 row
             const bool full_row = !STAR || (jj >= C::RY && jj < C::RY + C::H);
-            float in0[2 * C::RX + 1], in1[2 * C::RX + 1];
+            float v[10];
 #pragma unroll
-            for (int kx = 0; kx < 2 * C::RX + 1; ++kx) {
-              if (!full_row && kx != C::RX) continue;
-              in0[kx] = pl[jj * C::SX + kx];
-              in1[kx] = pl[jj * C::SX + 32 + kx];
+            for (int m = E0; m <= E1; ++m) {
+              if (!full_row && m != 2) continue;  // the centre columns are v[4], v[5]
+              const float2 t = *reinterpret_cast<const float2*>(pl + jj * C::SX + 2 * m);
+              v[2 * m] = t.x;
+              v[2 * m + 1] = t.y;
             }
 #pragma unroll
             for (int yy = 0; yy < C::H; ++yy) {
@@ -201,14 +208,14 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
                 for (int kx = 0; kx < 2 * C::RX + 1; ++kx) {
                   if (STAR && dy != 0 && kx != C::RX) continue;
                   const float wv = Wd[(dy + C::RY) * (2 * C::RX + 1) + kx];
-                  acc[yy][0] = fmaf(wv, in0[kx], acc[yy][0]);
-                  acc[yy][1] = fmaf(wv, in1[kx], acc[yy][1]);
+                  acc[yy][0] = fmaf(wv, v[4 - C::RX + kx], acc[yy][0]);
+                  acc[yy][1] = fmaf(wv, v[5 - C::RX + kx], acc[yy][1]);
                 }
               }
             }
           }
         }
-        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.pitch + xbase + lane;
+        float* o = args.dst + ((int64_t)z * args.ny + ybase) * args.pitch + xbase + 2 * lane;
         const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
         const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
 #pragma unroll
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(C::kThreads) stream3d_kernel(const __grid_cons
           if (yy < ylim) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-              if (lane + 32 * c < xlim) o[(size_t)yy * args.pitch + 32 * c] = acc[yy][c];
+              if (2 * lane + c < xlim) o[(size_t)yy * args.pitch + c] = acc[yy][c];
           }
       } else {
         float acc[C::H / 2][4];
