@@ -98,18 +98,24 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
     const int r0 = min((u / NS) * F::H, R - F::H);
     const int s0 = min((u % NS) * 8, S - 8);
     if (MODE == Mode::CudaCore) {
+      // lane l: columns 2l, 2l + 1 of the unit, inputs loaded as 8-byte
+      // pairs (v[e] = source column 8 s0 + 2l + e; the swizzle keeps pairs
+      // adjacent), as in the one-step kernel
+      constexpr int E0 = (4 - F::RX) / 2, E1 = (5 + F::RX) / 2;
       float acc[F::H][2];
 #pragma unroll
       for (int i = 0; i < F::H; ++i) acc[i][0] = acc[i][1] = 0.f;
       const float* pl = src + r0 * SP;
-      const int cb = 8 * s0 + kHaloX + c.lane - F::RX;  // first column read by this lane
+      const int cb = 8 * s0 + 2 * c.lane;  // first column this lane's pairs start at
 #pragma unroll
       for (int jj = 0; jj < F::H + 2 * F::RY; ++jj) {
-        float in0[2 * F::RX + 1], in1[2 * F::RX + 1];
+        float v[10];
 #pragma unroll
-        for (int k = 0; k < 2 * F::RX + 1; ++k) {
-          in0[k] = pl[jj * SP + (LV >= 2 ? swz(cb + k) : cb + k)];
-          in1[k] = pl[jj * SP + (LV >= 2 ? swz(cb + 32 + k) : cb + 32 + k)];
+        for (int m = E0; m <= E1; ++m) {
+          const int col = cb + 2 * m;
+          const float2 t = *reinterpret_cast<const float2*>(pl + jj * SP + (LV >= 2 ? swz(col) : col));
+          v[2 * m] = t.x;
+          v[2 * m + 1] = t.y;
         }
 #pragma unroll
         for (int yy = 0; yy < F::H; ++yy) {
@@ -118,8 +124,8 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
 #pragma unroll
             for (int k = 0; k < 2 * F::RX + 1; ++k) {
               const float wv = W[(dy + F::RY) * (2 * F::RX + 1) + k];
-              acc[yy][0] = fmaf(wv, in0[k], acc[yy][0]);
-              acc[yy][1] = fmaf(wv, in1[k], acc[yy][1]);
+              acc[yy][0] = fmaf(wv, v[4 - F::RX + k], acc[yy][0]);
+              acc[yy][1] = fmaf(wv, v[5 - F::RX + k], acc[yy][1]);
             }
           }
         }
@@ -128,24 +134,24 @@ __device__ __forceinline__ void fused_level(const FusedCtx& c, const float* src,
       const bool interior = gy0 >= 0 && gy0 + F::H <= (int)args.ny && gx0 >= 0 && gx0 + 64 <= (int)args.nx;
       if (LV < F::T) {
         float* d = dst + r0 * DP;
-        const int p0 = swz(8 * s0 + c.lane), p1 = swz(8 * s0 + c.lane + 32);
+        const int p0 = swz(8 * s0 + 2 * c.lane);  // the pair stays adjacent after the swizzle
 #pragma unroll
         for (int yy = 0; yy < F::H; ++yy)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const bool in = interior || ((unsigned)(gy0 + yy) < (unsigned)args.ny &&
-                                         (unsigned)(gx0 + c.lane + 32 * h) < (unsigned)args.nx);
-            d[yy * DP + (h ? p1 : p0)] = in ? acc[yy][h] : 0.f;
+                                         (unsigned)(gx0 + 2 * c.lane + h) < (unsigned)args.nx);
+            d[yy * DP + p0 + h] = in ? acc[yy][h] : 0.f;
           }
       } else {
-        float* o = args.dst + (int64_t)gy0 * args.pitch + gx0 + c.lane;
+        float* o = args.dst + (int64_t)gy0 * args.pitch + gx0 + 2 * c.lane;
 #pragma unroll
         for (int yy = 0; yy < F::H; ++yy)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const bool in = interior || ((unsigned)(gy0 + yy) < (unsigned)args.ny &&
-                                         (unsigned)(gx0 + c.lane + 32 * h) < (unsigned)args.nx);
-            if (in) o[(int64_t)yy * args.pitch + 32 * h] = acc[yy][h];
+                                         (unsigned)(gx0 + 2 * c.lane + h) < (unsigned)args.nx);
+            if (in) o[(int64_t)yy * args.pitch + h] = acc[yy][h];
           }
       }
     } else {

@@ -489,21 +489,26 @@ __global__ void __launch_bounds__(C::kThreads)
     const int ybase = y0 + wy * C::H;
     const int xbase = x0 + wx * 64;
     if (MODE == Mode::CudaCore) {
+      // FP32 FMA stencil: lane l computes columns 2l and 2l + 1 of its
+      // warp's 64 and loads the inputs of a row as 8-byte pairs (v[e] = tile
+      // row column 2l + e of the warp, e = 0..9; output column c reads
+      // v[c - 2l + 4 - r .. + r])
+      constexpr int E0 = (4 - C::RX) / 2, E1 = (5 + C::RX) / 2;
       float acc[C::H][2];
 #pragma unroll
       for (int i = 0; i < C::H; ++i) acc[i][0] = acc[i][1] = 0.f;
 #pragma unroll 1
       for (int dzi = 0; dzi < 2 * C::RZ + 1; ++dzi) {
         if (C::RZ != 0) load_operands(dzi);
-        const float* pl = S + (size_t)(wz + dzi) * C::SY * C::SX + (size_t)(wy * C::H) * C::SX + wx * 64 +
-                          kHaloX + lane - C::RX;
+        const float* pl = S + (size_t)(wz + dzi) * C::SY * C::SX + (size_t)(wy * C::H) * C::SX + wx * 64 + 2 * lane;
 #pragma unroll
         for (int jj = 0; jj < C::H + 2 * C::RY; ++jj) {
-          float in0[2 * C::RX + 1], in1[2 * C::RX + 1];
+          float v[10];
 #pragma unroll
-          for (int k = 0; k < 2 * C::RX + 1; ++k) {
-            in0[k] = pl[jj * C::SX + k];
-            in1[k] = pl[jj * C::SX + 32 + k];
+          for (int m = E0; m <= E1; ++m) {
+            const float2 t = *reinterpret_cast<const float2*>(pl + jj * C::SX + 2 * m);
+            v[2 * m] = t.x;
+            v[2 * m + 1] = t.y;
           }
 #pragma unroll
           for (int yy = 0; yy < C::H; ++yy) {
@@ -512,15 +517,15 @@ __global__ void __launch_bounds__(C::kThreads)
 #pragma unroll
               for (int k = 0; k < 2 * C::RX + 1; ++k) {
                 const float wv = W[(dy + C::RY) * (2 * C::RX + 1) + k];
-                acc[yy][0] = fmaf(wv, in0[k], acc[yy][0]);
-                acc[yy][1] = fmaf(wv, in1[k], acc[yy][1]);
+                acc[yy][0] = fmaf(wv, v[4 - C::RX + k], acc[yy][0]);
+                acc[yy][1] = fmaf(wv, v[5 - C::RX + k], acc[yy][1]);
               }
             }
           }
         }
       }
       if (z < args.nz) {
-        float* o = args.dst + (z * args.ny + ybase) * args.pitch + xbase + lane;
+        float* o = args.dst + (z * args.ny + ybase) * args.pitch + xbase + 2 * lane;
         const int pitch = (int)args.pitch;
         const int ylim = (int)(args.ny - ybase < C::H ? args.ny - ybase : C::H);
         const int xlim = (int)(args.nx - xbase < 64 ? args.nx - xbase : 64);
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(C::kThreads)
           if (yy < ylim) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-              if (lane + 32 * c < xlim) o[(size_t)yy * pitch + 32 * c] = acc[yy][c];
+              if (2 * lane + c < xlim) o[(size_t)yy * pitch + c] = acc[yy][c];
           }
         }
       }
