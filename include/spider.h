@@ -202,6 +202,23 @@ spider_status spider_run(spider_plan plan, const float* grid_in, float* grid_out
 spider_status spider_run_host(spider_plan plan, const float* host_in, float* host_out, int64_t steps,
                               cudaStream_t stream);
 
+/* spider_run_host_async -- spider_run_host without the wait, for a stream of
+ * host grids through one plan.  The paper has no counterpart: this is an
+ * addition of the library.  The call enqueues the copy of host_in into one
+ * of two plan-owned device slots (on a copy stream of the plan), the steps
+ * (on `stream`, after that copy) and the copy of the result to host_out (on
+ * a second copy stream, after the steps), and returns.  Successive calls use
+ * the two slots in turn, so the copies of one call overlap the steps of the
+ * call before it (with pinned host memory; pageable memory works but the
+ * copies then stage through the driver and overlap little).  host_in must
+ * stay unchanged and host_out untouched until spider_plan_sync(plan,
+ * stream) returns, which waits for the steps and for both copy streams;
+ * host_in and host_out must not be the same buffer.  Successive calls on one
+ * plan must pass the same `stream`.  The slots hold 4 * points floats of
+ * device memory from the first call until the plan is destroyed. */
+spider_status spider_run_host_async(spider_plan plan, const float* host_in, float* host_out, int64_t steps,
+                                    cudaStream_t stream);
+
 /* spider_run_static -- spider_run that allocates no device memory.
  * The paper has no counterpart: this is an addition of the library.
  *
@@ -232,8 +249,9 @@ spider_status spider_run_host(spider_plan plan, const float* host_in, float* hos
 spider_status spider_run_static(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
                                 cudaStream_t stream);
 
-/* Blocks until the plan's work on `stream` is done and reports any
- * device-side error (SPIDER_ERR_TIMEOUT for an expired wait). */
+/* Blocks until the plan's work on `stream` is done (and the copies of its
+ * spider_run_host_async calls) and reports any device-side error
+ * (SPIDER_ERR_TIMEOUT for an expired wait). */
 spider_status spider_plan_sync(spider_plan plan, cudaStream_t stream);
 
 /* spider_plan_error_bound -- the library's a priori bound on the relative L2

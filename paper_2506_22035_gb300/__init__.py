@@ -108,6 +108,17 @@ class Plan:
                                              _stream_handle(stream)), "spider_run_host")
         return out
 
+    def run_host_async(self, host_in: np.ndarray, steps: int, host_out: np.ndarray, stream=None) -> None:
+        """spider_run_host_async: enqueues copy in, steps and copy out and
+        returns; host_in and host_out (contiguous float32 arrays of the plan's
+        size, pinned for overlap) must stay alive and untouched until sync()."""
+        for arr in (host_in, host_out):
+            if arr.dtype != np.float32 or not arr.flags.c_contiguous or arr.size != self.points:
+                raise ValueError("host grids must be contiguous float32 arrays of the plan's size")
+        check(_native.load().spider_run_host_async(self._h, host_in.ctypes.data_as(ctypes.c_void_p),
+                                                   host_out.ctypes.data_as(ctypes.c_void_p), int(steps),
+                                                   _stream_handle(stream)), "spider_run_host_async")
+
     def sync(self, stream=None) -> None:
         check(_native.load().spider_plan_sync(self._h, _stream_handle(stream)), "spider_plan_sync")
 

@@ -41,6 +41,7 @@ SIGNATURES = {
                                      ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t)]),
     "spider_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "spider_run_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_run_static": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "spider_plan_sync": (c_int, [c_void_p, c_void_p]),
     "spider_plan_device_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),

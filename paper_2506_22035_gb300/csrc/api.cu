@@ -73,6 +73,15 @@ static void free_device(spider_plan_t* p) {
     dev_free(p, d.pad);
     dev_free(p, d.host_stage_in);
     dev_free(p, d.host_stage_out);
+    for (auto& h : d.host_slots) {
+      dev_free(p, h.in);
+      dev_free(p, h.out);
+      if (h.copied_in) cudaEventDestroy(h.copied_in);
+      if (h.stepped) cudaEventDestroy(h.stepped);
+      if (h.copied_out) cudaEventDestroy(h.copied_out);
+    }
+    if (d.h2d_stream) cudaStreamDestroy(d.h2d_stream);
+    if (d.d2h_stream) cudaStreamDestroy(d.d2h_stream);
     dev_free(p, d.status);
     drop_graphs(p);
     if (d.capture_stream) cudaStreamDestroy(d.capture_stream);
@@ -557,9 +566,60 @@ spider_status spider_run_host(spider_plan p, const float* host_in, float* host_o
   return SPIDER_OK;
 }
 
+spider_status spider_run_host_async(spider_plan p, const float* host_in, float* host_out, int64_t steps,
+                                    cudaStream_t stream) {
+  set_error("");
+  if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
+  if (!host_in || !host_out) return fail(SPIDER_ERR_INVALID, "host pointer is NULL");
+  if (steps < 0) return fail(SPIDER_ERR_INVALID, "steps must be >= 0");
+  std::lock_guard<std::mutex> lock(p->mu);
+  spider_status s = ensure_device(p);
+  if (s != SPIDER_OK) return s;
+  DeviceState& d = p->dev;
+  const size_t bytes = (size_t)p->points() * sizeof(float);
+  if (!d.h2d_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&d.h2d_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d.d2h_stream, cudaStreamNonBlocking);
+    for (auto& h : d.host_slots) {
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.copied_in, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.stepped, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.copied_out, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host pipeline streams and events");
+  }
+  DeviceState::HostSlot& h = d.host_slots[d.host_next];
+  if (!h.in) {
+    cudaError_t e = dev_alloc(p, reinterpret_cast<void**>(&h.in), bytes);
+    if (e == cudaSuccess) e = dev_alloc(p, reinterpret_cast<void**>(&h.out), bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPIDER_ERR_OOM, "device grids for host run");
+    }
+  }
+  d.host_next ^= 1;
+  // the slot's input grid was last read by the steps of the call two back,
+  // its output grid by that call's copy back
+  if (h.used) SPIDER_CUDA(cudaStreamWaitEvent(d.h2d_stream, h.stepped, 0));
+  SPIDER_CUDA(cudaMemcpyAsync(h.in, host_in, bytes, cudaMemcpyHostToDevice, d.h2d_stream));
+  SPIDER_CUDA(cudaEventRecord(h.copied_in, d.h2d_stream));
+  SPIDER_CUDA(cudaStreamWaitEvent(stream, h.copied_in, 0));
+  if (h.used) SPIDER_CUDA(cudaStreamWaitEvent(stream, h.copied_out, 0));
+  s = run_cached(p, h.in, h.out, steps, stream);
+  if (s != SPIDER_OK) return s;
+  SPIDER_CUDA(cudaEventRecord(h.stepped, stream));
+  SPIDER_CUDA(cudaStreamWaitEvent(d.d2h_stream, h.stepped, 0));
+  SPIDER_CUDA(cudaMemcpyAsync(host_out, h.out, bytes, cudaMemcpyDeviceToHost, d.d2h_stream));
+  SPIDER_CUDA(cudaEventRecord(h.copied_out, d.d2h_stream));
+  h.used = true;
+  return SPIDER_OK;
+}
+
 spider_status spider_plan_sync(spider_plan p, cudaStream_t stream) {
   if (!p) return fail(SPIDER_ERR_INVALID, "plan is NULL");
   SPIDER_CUDA(cudaStreamSynchronize(stream));
+  // the copies of spider_run_host_async calls (their steps ran on `stream`)
+  if (p->dev.h2d_stream) SPIDER_CUDA(cudaStreamSynchronize(p->dev.h2d_stream));
+  if (p->dev.d2h_stream) SPIDER_CUDA(cudaStreamSynchronize(p->dev.d2h_stream));
   if (p->dev.status) {
     int status = 0;
     SPIDER_CUDA(cudaMemcpy(&status, p->dev.status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -597,6 +657,8 @@ spider_status spider_plan_device_bytes(spider_plan p, size_t* bytes) {
   if (d.scratch) b += d.scratch_bytes;
   if (d.pad) b += d.pad_bytes;
   if (d.host_stage_in) b += 2 * (size_t)p->points() * sizeof(float);
+  for (const auto& h : d.host_slots)
+    if (h.in) b += 2 * (size_t)p->points() * sizeof(float);
   *bytes = b;
   return SPIDER_OK;
 }

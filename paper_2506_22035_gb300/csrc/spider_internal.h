@@ -84,6 +84,19 @@ struct DeviceState {
   size_t pad_bytes = 0;
   float* host_stage_in = nullptr;  // device grids for spider_run_host
   float* host_stage_out = nullptr;
+  // spider_run_host_async: two staging slots used in turn, so one call's
+  // copies overlap the steps of the call before it; the copies run on two
+  // streams of the plan (one per direction), ordered against the steps by
+  // events
+  struct HostSlot {
+    float* in = nullptr;
+    float* out = nullptr;
+    cudaEvent_t copied_in = nullptr, stepped = nullptr, copied_out = nullptr;
+    bool used = false;
+  };
+  HostSlot host_slots[2];
+  int host_next = 0;
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
   int* status = nullptr;           // device error word (0 = ok)
   size_t scratch_bytes = 0;
   // Stream-ordered allocation (the serving loop): when `pool` is set, every

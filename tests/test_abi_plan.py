@@ -636,3 +636,18 @@ def test_one_step_comparator_engines_are_2d_tf32_only(lib, engine):
             p.set_engine(engine)
         assert e.value.status == _native.SPIDER_ERR_UNSUPPORTED
         p.close()
+
+
+def test_run_host_async_rejects_bad_arguments_without_touching_a_device(lib):
+    import stencil_inputs as si
+    buf = np.zeros(40 * 72, np.float32)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    assert lib.spider_run_host_async(None, ptr, ptr, 1, None) == _native.SPIDER_ERR_INVALID
+    p = spider.Plan(si.normalised_coeffs(2, 1, "box", si.rng(32, 0)), (40, 72), "box", "tf32")
+    assert lib.spider_run_host_async(p.handle, None, ptr, 1, None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_run_host_async(p.handle, ptr, None, 1, None) == _native.SPIDER_ERR_INVALID
+    assert lib.spider_run_host_async(p.handle, ptr, ptr, -1, None) == _native.SPIDER_ERR_INVALID
+    size = ctypes.c_size_t(1)
+    assert lib.spider_plan_device_bytes(p.handle, ctypes.byref(size)) == 0
+    assert size.value == 0                      # nothing was allocated
+    p.close()

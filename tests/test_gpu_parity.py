@@ -677,6 +677,31 @@ def test_batch_replay_follows_changed_step_counts():
         p.close()
 
 
+def test_run_host_async_stream_of_grids():
+    # a stream of host grids through one plan: copies on the plan's copy
+    # streams overlap the previous call's steps; every result equals the
+    # device run of the same grid and step count, bit for bit
+    g = si.rng(33, 0)
+    w = si.normalised_coeffs(2, 2, "box", g)
+    shape = (300, 520)
+    plan = spider.Plan(w, shape, "box", "tf32")
+    grids = [si.grid(shape, -1, 1, si.rng(33, k + 1)) for k in range(5)]
+    counts = [3, 8, 1, 0, 5]
+    pinned_in = [torch.from_numpy(u).pin_memory() for u in grids]
+    pinned_out = [torch.full_like(t, float("nan")).pin_memory() for t in pinned_in]
+    for k in range(5):
+        plan.run_host_async(pinned_in[k].numpy(), counts[k], pinned_out[k].numpy())
+    plan.sync()
+    for k in range(5):
+        a = torch.from_numpy(grids[k]).cuda()
+        b = torch.empty_like(a)
+        plan.run(a, b, counts[k])
+        plan.sync()
+        assert np.array_equal(pinned_out[k].numpy(), b.cpu().numpy()), k
+    assert np.array_equal(pinned_in[0].numpy(), grids[0])       # input preserved
+    plan.close()
+
+
 def _offset_view(t, off):
     """A copy of `t` that starts `off` floats into its own allocation (a base
     address that is not 16-byte aligned when off % 4 != 0)."""
