@@ -144,3 +144,27 @@ def test_box2d_r3_8192_full_grid_error(box2d_reference, prec):
     assert rel <= BOX2D_FULL_TOL[prec], (prec, rel)
     assert rel <= plan.error_bound(wl.steps)
     plan.close()
+
+
+# full-grid errors measured on GB300 (Heat-3D 4.0e-4, Box-3D 1.3e-4 after 50
+# steps in TF32) and the tolerances, about three times measured
+BOX3D_FULL_TOL = {"heat3d": 1.2e-3, "box3d": 4e-4}
+
+
+@pytest.mark.parametrize("name", ["heat3d", "box3d"])
+def test_3d_512_full_grid_error(name):
+    # the 3-D benchmark workloads at full size and step count, autotuned as
+    # bench.py runs them; relative L2 error of the whole grid in FP64 on the GPU
+    wl = si.HEAT3D_512 if name == "heat3d" else si.BOX3D_512
+    u0, w = si.workload_inputs(wl)
+    ref = torch.from_numpy(oracle.stencil(u0, w, wl.steps)).cuda()
+    plan = spider.Plan(w, u0.shape, wl.shape, "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    plan.autotune(a, b, wl.steps)
+    plan.run(a, b, wl.steps)
+    plan.sync()
+    rel = spider.relative_l2_error(b, ref)
+    assert rel <= BOX3D_FULL_TOL[name], (name, rel)
+    assert rel <= plan.error_bound(wl.steps)
+    plan.close()

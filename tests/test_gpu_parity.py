@@ -702,6 +702,39 @@ def test_run_host_async_stream_of_grids():
     plan.close()
 
 
+def test_batched_mix_full_size_matches_lone_runs():
+    # the benchmark's 64-grid mix (sides 256..4096, r 1..3, 10..200 steps) in
+    # one spider_batch call, in the default routing the bench times: every
+    # grid bit for bit its plan's own run, on the first call and on the
+    # replayed one; the cheapest job also against the oracle
+    jobs = si.batched_jobs()
+    plans, ins, outs = [], [], []
+    for jb in jobs:
+        u0, w = si.job_inputs(jb)
+        plans.append(spider.Plan(w, jb.extents, jb.shape, "tf32"))
+        ins.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.full_like(ins[-1], float("nan")))
+    steps = [jb.steps for jb in jobs]
+    refs = []
+    for p, x, n in zip(plans, ins, steps):
+        y = torch.empty_like(x)
+        p.run(x, y, n)
+        refs.append(y)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for o in outs:
+            o.fill_(float("nan"))
+        spider.batch(plans, ins, outs, steps)
+        torch.cuda.synchronize()
+        for k in range(len(jobs)):
+            assert torch.equal(outs[k], refs[k]), (k, jobs[k].extents, jobs[k].steps)
+    k = min(range(len(jobs)), key=lambda i: int(np.prod(jobs[i].extents)) * jobs[i].steps)
+    u0, w = si.job_inputs(jobs[k])
+    check_close(outs[k].cpu().numpy(), oracle.stencil(u0, w, jobs[k].steps), ("sparse_tc", "tf32"))
+    for p in plans:
+        p.close()
+
+
 def _offset_view(t, off):
     """A copy of `t` that starts `off` floats into its own allocation (a base
     address that is not 16-byte aligned when off % 4 != 0)."""
