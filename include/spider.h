@@ -166,6 +166,23 @@ spider_status spider_plan_set_tile_variant(spider_plan plan, int variant);
 spider_status spider_plan_autotune(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
                                    cudaStream_t stream, int* steps_per_pass, int* variant);
 
+/* spider_plan_autotune_arithmetic -- the split-depth part of the autotuner
+ * (the paper states no precision; this is an addition of the library).
+ * Among the arithmetics the library builds for the plan's stencil -- sparse
+ * TF32, the FP16 hi/lo split (only when every |grid_in| value is below
+ * 16384), the BF16 hi/mid/lo split, FP32 on CUDA cores -- it keeps those
+ * whose a priori error bound for `steps` steps (spider_plan_error_bound)
+ * meets err_target, autotunes each on the caller's grids (as
+ * spider_plan_autotune, on a temporary plan), times `steps` steps of each
+ * twice with CUDA events on `stream`, and returns the fastest in *prec /
+ * *engine and its rate in *gstencil_s (GStencil/s; all nullable).  The plan
+ * itself is not changed: create a plan in the chosen precision (and set its
+ * engine) to run in it.  grid_out is overwritten.  Synchronous.
+ * SPIDER_ERR_UNSUPPORTED when no arithmetic's bound meets the target. */
+spider_status spider_plan_autotune_arithmetic(spider_plan plan, const float* grid_in, float* grid_out, int64_t steps,
+                                              double err_target, cudaStream_t stream, spider_precision* prec,
+                                              spider_engine* engine, double* gstencil_s);
+
 /* Reads back the plan's packed operands (host copies) for inspection and
  * testing.  Any pointer may be NULL; sizes are in 32-bit words.
  *   n_operand_words / operand_words : tensor-core A fragments, per

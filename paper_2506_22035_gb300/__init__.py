@@ -78,6 +78,19 @@ class Plan:
               "spider_plan_autotune")
         return t.value, v.value
 
+    def autotune_arithmetic(self, grid_in, grid_out, steps: int, err_target: float, stream=None):
+        """spider_plan_autotune_arithmetic: the fastest arithmetic whose a
+        priori error bound for `steps` steps meets err_target, timed on these
+        grids; returns (precision, engine, GStencil/s).  The plan is unchanged."""
+        pr, en, rate = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(_native.load().spider_plan_autotune_arithmetic(self._h, _ptr(grid_in), _ptr(grid_out), int(steps),
+                                                             float(err_target), _stream_handle(stream),
+                                                             ctypes.byref(pr), ctypes.byref(en), ctypes.byref(rate)),
+              "spider_plan_autotune_arithmetic")
+        prec = {v: k for k, v in PRECISIONS.items()}[pr.value]
+        engine = {v: k for k, v in ENGINES.items()}[en.value]
+        return prec, engine, rate.value
+
     def operands(self):
         lib = _native.load()
         na, nm = ctypes.c_size_t(), ctypes.c_size_t()

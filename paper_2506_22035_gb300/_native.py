@@ -37,6 +37,9 @@ SIGNATURES = {
     "spider_plan_set_tile_variant": (c_int, [c_void_p, c_int]),
     "spider_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int),
                                      ctypes.POINTER(c_int)]),
+    "spider_plan_autotune_arithmetic": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_double, c_void_p,
+                                                ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                                ctypes.POINTER(ctypes.c_double)]),
     "spider_plan_operands": (c_int, [c_void_p, ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t),
                                      ctypes.POINTER(c_uint32), c_size_t, ctypes.POINTER(c_size_t)]),
     "spider_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),

@@ -651,3 +651,17 @@ def test_run_host_async_rejects_bad_arguments_without_touching_a_device(lib):
     assert lib.spider_plan_device_bytes(p.handle, ctypes.byref(size)) == 0
     assert size.value == 0                      # nothing was allocated
     p.close()
+
+
+def test_autotune_arithmetic_rejects_bad_arguments_without_touching_a_device(lib):
+    import stencil_inputs as si
+    buf = np.zeros(40 * 72, np.float32)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    pr, en, rate = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    args = (ctypes.byref(pr), ctypes.byref(en), ctypes.byref(rate))
+    assert lib.spider_plan_autotune_arithmetic(None, ptr, ptr, 10, 1e-3, None, *args) == _native.SPIDER_ERR_INVALID
+    p = spider.Plan(si.normalised_coeffs(2, 1, "box", si.rng(34, 0)), (40, 72), "box", "tf32")
+    for steps, target in ((0, 1e-3), (10, 0.0), (10, -1.0), (10, float("nan")), (10, float("inf"))):
+        assert lib.spider_plan_autotune_arithmetic(p.handle, ptr, ptr, steps, target, None, *args) == \
+            _native.SPIDER_ERR_INVALID, (steps, target)
+    p.close()

@@ -168,3 +168,42 @@ def test_3d_512_full_grid_error(name):
     assert rel <= BOX3D_FULL_TOL[name], (name, rel)
     assert rel <= plan.error_bound(wl.steps)
     plan.close()
+
+
+@pytest.mark.parametrize("target", [1e-2, 1e-5, 1e-6])
+def test_autotune_arithmetic_meets_the_error_target(target):
+    # the split-depth autotuner: the fastest arithmetic whose a priori bound
+    # meets the target; running in it meets the target against the oracle
+    g = si.rng(71, 0)
+    u0 = si.grid((512, 512), -1, 1, g)
+    w = si.normalised_coeffs(2, 2, "box", si.rng(71, 1))
+    steps = 50
+    plan = spider.Plan(w, u0.shape, "box", "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    prec, engine, rate = plan.autotune_arithmetic(a, b, steps, target)
+    assert rate > 0
+    assert plan.error_bound(steps, prec, engine) <= target
+    if target >= 1e-2:
+        assert (prec, engine) == ("tf32", "sparse_tc")   # the fastest, and its bound meets 1e-2
+    got, chosen = run(u0, w, "box", prec, engine, steps)
+    chosen.close()
+    ref = oracle.stencil(u0, w, steps)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= target, (prec, engine)
+    with pytest.raises(spider.SpiderError) as e:
+        plan.autotune_arithmetic(a, b, steps, 1e-12)         # no arithmetic's bound is that small
+    assert e.value.status == 2
+    plan.close()
+
+
+def test_autotune_arithmetic_keeps_large_values_out_of_fp16():
+    # values of 2e4 do not fit the FP16 split: a 1e-5 target goes elsewhere
+    g = si.rng(72, 0)
+    u0 = (si.grid((256, 256), -1, 1, g) * 2e4).astype(np.float32)
+    w = si.normalised_coeffs(2, 1, "box", si.rng(72, 1))
+    plan = spider.Plan(w, u0.shape, "box", "tf32")
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    prec, engine, _ = plan.autotune_arithmetic(a, b, 20, 1e-5)
+    assert prec != "f16x2"
+    plan.close()
