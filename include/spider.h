@@ -311,9 +311,11 @@ void spider_plan_destroy(spider_plan plan);
  * issued as a CUDA graph: work items (pass, grid, tile) are claimed from a
  * device queue in pass-major order, and pass p of a tile starts only after
  * the tile and its eight neighbours finished pass p-1 (per-tile counters,
- * bounded waits).  A pass is two time steps on a (64 - 2r) x 120 tile (the
- * first or last pass one step when the step count needs it), or one step on
- * a 64 x 128 tile for one-step grids; see spider_batch_configure.  Results
+ * bounded waits).  A pass is two time steps on a (56 - 2r) x 120 tile (the
+ * first or last pass one step when the step count needs it, and every pass
+ * of a one-step grid), see spider_batch_configure; seven warps compute the
+ * tiles while an eighth claims the items and loads their boxes, three
+ * CTAs per SM.  Results
  * are bit-identical to spider_run's.  Such grids of at least 2^16 points
  * and more than one step run through spider_run with fused passes instead
  * (the plan's steps per pass and tile variant if it fuses, else the
@@ -337,7 +339,7 @@ spider_status spider_batch(int n, const spider_plan* plans, const float* const* 
  * fuse_min_points points (with more than one step) run as fused passes of
  * their own on side streams; smaller grids run in the persistent queue, whose
  * items take queue_steps_per_item time steps (1, or 2: the fused kernel's two
- * levels on tiles of (64 - 2r) x 120 outputs).  0 restores a default (the
+ * levels on tiles of (56 - 2r) x 120 outputs).  0 restores a default (the
  * measured best: 2^16 points, 2 steps per item).  Process-wide; applies to
  * later calls. */
 spider_status spider_batch_configure(long long fuse_min_points, int queue_steps_per_item);

@@ -3,23 +3,22 @@
 // a device work queue; larger grids run as fused multi-step passes of their
 // own on side streams beside it (see kFuseMinPoints).
 //
-// Queue work items are (pass p, job, tile) in pass-major order; CTAs claim
-// them with one atomic counter.  A pass is two time steps on the fused
-// kernel's level scheme (output tile (64 - 2r) x 120, level 1 of 64 x 128 in
-// shared memory, input box (64 + 2r) x 136), or one step: the first pass of
-// a job whose step count is odd or whose input rows TMA cannot describe, the
-// last when one step is left, and every pass of a one-step job (64 x 128
-// tile of stencil_step_kernel) or when spider_batch_configure asks for one
-// step per item.  Item (p, j, tile) reads job j's grid after pass p-1 over
-// the tile plus a halo narrower than a tile, so it may start only after the
-// tile and its eight neighbours have finished pass p-1 (those are also the
-// last readers of the buffer it overwrites).  Each job keeps one completion
-// counter per tile; a producer warp waits on the neighbours' counters with
-// bounded spins (acquire loads) and publishes a tile's counter with a
-// release store once every consumer warp has handed the tile's stage back.
-// Because every CTA claims and processes its items in global order and an
-// item only waits on items of an earlier pass, every awaited item is already
-// held by a running CTA: the queue cannot deadlock, whatever the residency.
+// Queue work items are (pass p, job, tile); CTAs claim them with one atomic
+// counter, in pass-major order.  Every item runs the fused kernel's level
+// scheme on a tile of (56 - 2r) x 120 outputs: a two-step pass computes
+// level 1 (56 x 128) into shared memory and level 2 into the grid from one
+// input box of (56 + 2r) x 136 points; a one-step pass (the first pass of a
+// job whose step count is odd or whose input rows TMA cannot describe, the
+// last when one step is left, every pass of a one-step job, or every pass
+// when spider_batch_configure asks for one step per item) computes one level
+// from a 56 x 128 box.  Item (p, j, tile) reads job j's grid after pass p-1
+// over the tile plus a halo narrower than a tile, so it may start only after
+// the tile and its eight neighbours have finished pass p-1 (those are also
+// the last readers of the buffer it overwrites).  Each job keeps one
+// completion counter per tile; the producer warp tests the neighbours'
+// counters (acquire loads) and publishes a tile's counter with a release
+// store once the consumer warps have stored the tile.  The deadlock-freedom
+// argument is at batch_kernel.
 //
 // Each job brings its own tensor maps and packed operands (TF32 sparse MMA).
 #include <algorithm>
@@ -42,23 +41,45 @@ spider_status run_cached(spider_plan_t* p, const float* in, float* out, int64_t 
 
 namespace {
 
-constexpr int kBY = 64, kBX = 128, kWarpsY = 4, kWarpsX = 2, kH = 16;
-constexpr int kThreads = kWarpsY * kWarpsX * 32;
-constexpr int kMaxStageFloats = (kBY + 2 * kMaxR) * (kBX + 2 * kHaloX);
+// Every queue item runs the fused kernel's level scheme on a tile of
+// (56 - 2r) x 120 outputs, one or two time steps: level 1 of a two-step item
+// is 56 x 128, i.e. 7 x 2 warp units of 8 rows x 64 columns, two for each of
+// the seven consumer warps (level 2 and one-step items: 7 x 2 units as
+// well).  Seven consumer warps and one producer warp make 256 threads, so
+// three CTAs per SM keep 80 registers a thread, the stand-alone fused
+// kernel's budget (with a ninth warp the cap of 72 made the tile code spill).
+constexpr int kConsumerWarps = 7;
+constexpr int kThreads = kConsumerWarps * 32;  // consumer threads
+constexpr int kQueueThreads = kThreads + 32;    // and one producer warp
+constexpr int kTileL1 = 56;                     // rows of level 1 (two-step) / of the box (one-step)
+// The largest box: a two-step pass, (56 - 2r + 4r) x (120 + 16) points.
+constexpr int kMaxStageFloats = (kTileL1 + 2 * kMaxR) * (120 + 4 * kHaloX);
 constexpr int kStageStride = (kMaxStageFloats * 4 + 1023) / 1024 * 1024;
-// stages, alignment, barriers and slots, the level buffer of two-step items
-constexpr int kSmemBase = 2 * kStageStride + 1024 + 128 + 64 * 128 * 4;
-// queue tables go to shared memory only while two CTAs still fit on an SM
+constexpr int kLevelFloats = kTileL1 * 128;  // level 1 of a two-step pass (pitch 128)
+// Shared memory: one stage | level buffer | the current job's packed
+// operands (A words, metadata) and record | barriers and slot | tables.
+constexpr int kOpsABytes = (2 * kMaxR + 2) * 32 * 16;  // uint4 per lane per A index
+constexpr int kOpsEBytes = (2 * kMaxR + 2) * 32 * 4;   // metadata word per lane per A index
+constexpr int kJobBytes = 256;                         // >= sizeof(BatchJob), checked below
+constexpr int kLevelOff = kStageStride;
+constexpr int kOpsOff = kLevelOff + kLevelFloats * 4;
+constexpr int kJobOff = kOpsOff + kOpsABytes + kOpsEBytes;
+constexpr int kBarOff = kJobOff + kJobBytes;
+constexpr int kTablesOff = kBarOff + 128;
+constexpr int kSmemBase = kTablesOff + 1024;  // + alignment slack
+// queue tables go to shared memory only while three CTAs still fit on an SM
 constexpr int kMaxTableSmem = 3 * 1024;
-static_assert(2 * (kSmemBase + kMaxTableSmem + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(3 * (kSmemBase + kMaxTableSmem + 1024) <= 228 * 1024, "three CTAs per SM");
 // Grids of at least this many points (with more than one step) run as fused
 // passes of their own on side streams; smaller ones, and single steps, go
 // through the persistent queue.  Measured on the mixed batch of 64 grids of
 // 256^2..4096^2 (GStencil/s, replayed), with two fused steps per queue item:
-// threshold 2^20: 1026, 2^18: 1066, 2^17: 1045, 2^16 (every grid of the mix
-// fused): 1118, every grid in the queue: 883 -- the side streams run each
-// grid with its own tuned tile and depth.  Below it the queue wins: 256 grids
-// of 32^2..255^2 points run at 244 GStencil/s through it and at 41 as fused
+// 2^16 (every grid of the mix fused): 1120, every grid in the queue: 957
+// (an earlier queue kernel: 2^20: 1026, 2^18: 1066, 2^17: 1045).  A fused
+// pass is statically scheduled, while a queue item pays a claim, a
+// dependency test and a hand-over, and consecutive passes of one job on a
+// side stream find its grids in L2.  Below it the queue wins: 256 grids of
+// 32^2..255^2 points run at 278 GStencil/s through it and at 41 as fused
 // passes on side streams (grids of a few tiles are all launch latency).
 constexpr long long kFuseMinPoints = 1LL << 16;
 constexpr int kQueueStepsPerItem = 2;
@@ -142,15 +163,14 @@ struct SideJoin {
 // pass but the first then loads through TMA, and only the first pass's halo
 // boxes are loaded by the consumers (`tma0` = 0).
 //
-// A job with `two` = 0 takes one step per pass on 64 x 128 tiles.  A job
-// with `two` = 1 takes two steps per pass on the fused kernel's tiles of
-// (64 - 2r) x 120 outputs: level 1, grown by r rows and 4 columns on each
-// side, goes to shared memory, level 2 to the grid, from one input box of
-// (64 + 2r) x 136 points -- the one-step box.  Its first pass takes a single
-// step when the step count is odd or the consumers load it (`head1`), and
-// its last a single step when what is left is odd (`tail1`), on the same
-// tiles.
-struct BatchJob {
+// Every job runs on tiles of (56 - 2r) x 120 outputs.  A job with `two` = 0
+// takes one step per pass (a 56 x 128 box).  A job with `two` = 1 takes two
+// steps per pass: level 1, grown by r rows and 4 columns on each side, goes
+// to shared memory, level 2 to the grid, from one input box of (56 + 2r) x
+// 136 points.  Its first pass takes a single step when the step count is odd
+// or the consumers load it (`head1`), and its last a single step when what
+// is left is odd (`tail1`), on the same tiles.
+struct alignas(16) BatchJob {  // 16-byte multiple: records are bulk-copied
   int64_t nx, ny;
   int64_t pitch;       // row pitch of bufs (floats)
   int r;
@@ -172,6 +192,8 @@ struct BatchJob {
   int tma0;            // 1: `in` is TMA-describable; 0: consumers load the first pass's boxes
 };
 
+static_assert(sizeof(BatchJob) <= kJobBytes && sizeof(BatchJob) % 16 == 0, "job record copy");
+
 // Steps of pass p of a job.
 __host__ __device__ inline int pass_steps(const BatchJob& jb, int p) {
   if (!jb.two) return 1;
@@ -180,17 +202,15 @@ __host__ __device__ inline int pass_steps(const BatchJob& jb, int p) {
   return 2;
 }
 
+// Two-step pass and one-step pass on the queue tile of radius R: the output
+// tile is (56 - 2R) x 120; level 1 of the two-step pass is 56 x 128.
 template <int R>
-using BatchTile = TileCfg<0, R, R, 1, kWarpsY, kWarpsX, kH>;
-// Two-step pass and one-step pass on the fused tile of radius R: the output
-// tile is (64 - 2R) x 120; level 1 of the two-step pass is 64 x 128.
+using BatchFused2 = FuseCfg<R, 2, kTileL1 - 2 * R, 120, 8, kConsumerWarps>;
 template <int R>
-using BatchFused2 = FuseCfg<R, 2, 64 - 2 * R, 120, 8, kWarpsY * kWarpsX>;
-template <int R>
-using BatchFused1 = FuseCfg<R, 1, 64 - 2 * R, 120, 8, kWarpsY * kWarpsX>;
-constexpr int kLevelFloats = 64 * 128;  // level 1 of a two-step pass (pitch 128)
+using BatchFused1 = FuseCfg<R, 1, kTileL1 - 2 * R, 120, 8, kConsumerWarps>;
 static_assert(BatchFused2<1>::kPStride == kLevelFloats * 4 && BatchFused2<3>::kPStride == kLevelFloats * 4,
               "level buffer");
+static_assert(BatchFused2<kMaxR>::kInBytes <= kStageStride && BatchFused1<1>::kInBytes <= kStageStride, "stage");
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -201,59 +221,27 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One tile of one step: operands to registers, MMAs, write-back.  Every step
-// but a job's last stores its outputs rounded to TF32 (`out_tf32`), so the
-// steps after the first read operands that need no rounding (RIN = false);
-// the MMA sees the same values either way.
-// A8 / E8 hold the job's packed operands (the first 2R + 2 entries).
-constexpr int kNA = 2 * kMaxR + 2;
-template <int R, bool RIN>
-__device__ __forceinline__ void batch_tile(const BatchJob& jb, const uint4 (&A8)[kNA], const uint32_t (&E8)[kNA],
-                                           const float* S, float* dst, int64_t pitch, int x0, int y0,
-                                           bool out_tf32) {
-  using C = BatchTile<R>;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, q = lane & 3;
-  const int wx = warp % C::WX, wy = warp / C::WX;
-  uint4 A[C::NA];
-  uint32_t E[C::NA];
-#pragma unroll
-  for (int a = 0; a < C::NA; ++a) {
-    A[a] = A8[a];
-    E[a] = E8[a];
-  }
-  float acc[C::H / 2][4];
-#pragma unroll
-  for (int i = 0; i < C::H / 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  const float* row0 = S + (size_t)(wy * C::H) * C::SX + wx * 64 + 8 * g + 4 * ((q == 1) ? 2 : (q == 2) ? 1 : q);
-  plane_sp_tf32<C, C::SX, RIN>(row0, A, E, acc);
-  if (out_tf32) round_tf32_inplace(acc);
-  const int ybase = y0 + wy * C::H, xbase = x0 + wx * 64;
-  float* o = dst + (int64_t)ybase * pitch + xbase + 16 * q + g;
-  const int ylim = (int)(jb.ny - ybase < C::H ? jb.ny - ybase : C::H);
-  const int xlim = (int)(jb.nx - xbase < 64 ? jb.nx - xbase : 64);
-#pragma unroll
-  for (int pp = 0; pp < C::H / 2; ++pp)
-#pragma unroll
-    for (int sr = 0; sr < 2; ++sr)
-      if (2 * pp + sr < ylim) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          if (16 * q + 8 * c + g < xlim) o[(size_t)(2 * pp + sr) * pitch + 8 * c] = acc[pp][2 * sr + c];
-      }
+constexpr int kNA = 2 * kMaxR + 2;  // packed A operands of the largest radius
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One pass of a two-step job on the fused tile at (x0, y0): STEPS = 2 runs
-// level 1 from the staged box into the shared level buffer P and level 2
-// into the grid; STEPS = 1 runs one level from the box into the grid.  The
-// consumer warps synchronise among themselves (named barrier 1), not with
-// the producer warps.
+// One pass of a job on the fused tile at (x0, y0): STEPS = 2 runs level 1
+// from the staged box into the shared level buffer P and level 2 into the
+// grid; STEPS = 1 runs one level from the box into the grid.  Every step but
+// a job's last stores its outputs rounded to TF32 (`out_tf32`), so the steps
+// after the first read operands that need no rounding (RIN = false); the MMA
+// sees the same values either way.  A8 / E8 hold the job's packed operands
+// (the first 2R + 2 entries).  The consumer warps synchronise among
+// themselves (named barrier 1), not with the producer warp: once every
+// consumer has read the box, thread 0 arrives on `boxfree` (the producer may
+// load the next item's box into the stage), and once every consumer has
+// stored its outputs, on `done` (the producer publishes the tile).
 template <int R, int STEPS, bool RIN>
 __device__ __forceinline__ void batch_fused(const BatchJob& jb, const uint4 (&A8)[kNA], const uint32_t (&E8)[kNA],
                                             const float* S, float* P, float* dst, int64_t pitch, int x0, int y0,
-                                            bool out_tf32, int* status) {
+                                            bool out_tf32, int* status, uint64_t* boxfree, uint64_t* done) {
   using F = typename std::conditional<STEPS == 2, BatchFused2<R>, BatchFused1<R>>::type;
   uint4 A[F::NA];
   uint32_t E[F::NA];
@@ -284,11 +272,18 @@ __device__ __forceinline__ void batch_fused(const BatchJob& jb, const uint4 (&A8
   c.q = c.lane & 3;
   if constexpr (STEPS == 2) {
     fused_level<F, Mode::SpTF32, RIN, 1>(c, S, P, A, E, Ad, Am, Em, W);
-    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // level 1 complete in P
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // level 1 complete in P, box read
+    if (threadIdx.x == 0) mbar_arrive(boxfree);
     fused_level<F, Mode::SpTF32, RIN, 2>(c, P, nullptr, A, E, Ad, Am, Em, W);
-    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // P is free for the next item
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // stores issued, P free for the next item
+    if (threadIdx.x == 0) mbar_arrive(done);
   } else {
     fused_level<F, Mode::SpTF32, RIN, 1>(c, S, nullptr, A, E, Ad, Am, Em, W);
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+    if (threadIdx.x == 0) {
+      mbar_arrive(boxfree);
+      mbar_arrive(done);
+    }
   }
 }
 
@@ -331,32 +326,211 @@ __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// kThreads consumer threads (8 warps) compute tiles; two producer warps, one
-// per stage of a two-stage ring, claim items, wait for their dependencies and
-// issue their TMA loads, so the queue latency of two items overlaps the
-// tensor-core work.  Claims stay in the order the consumers process the
-// stages (a shared turn counter), so every CTA processes its items in claim
-// order, which keeps the queue free of deadlock (see above).
-// The queue tables (job records, job order, step offsets, jobs active per
-// step, tile prefix sums) are one contiguous block `tables` of `tables_bytes`
-// bytes whose parts start at the given offsets.  When `tables_in_smem` is set
-// the CTA copies the block into shared memory first, so claiming and decoding
-// an item costs one global atomic and no other global round trip.
-__global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned char* __restrict__ tables,
+// The producer warp's view of one claimed item.
+struct Claim {
+  int end, skip;  // past the last item / left out (spider_batch_drop_item)
+  int job, s, tile, tx, ty;
+};
+
+// Claims the next queue item (one global atomic by lane 0) and decodes it
+// into (job, pass, tile) with a warp-parallel search of the entry table.
+__device__ __forceinline__ Claim claim_item(int* counter, long long total, const long long* __restrict__ ent_prefix,
+                                            const int2* __restrict__ ent, int n_ent,
+                                            const BatchJob* __restrict__ jobs, long long drop_item, int lane) {
+  long long item = 0;
+  if (lane == 0) item = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ULL);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  Claim c = {};
+  c.end = item >= total;
+  if (c.end) return c;
+  const int e = warp_search(ent_prefix, n_ent, item, lane);
+  const int2 je = ent[e];
+  c.job = je.x;
+  c.s = je.y;
+  c.tile = (int)(item - ent_prefix[e]);
+  c.tx = c.tile % jobs[c.job].tiles_x;
+  c.ty = c.tile / jobs[c.job].tiles_x;
+  c.skip = item == drop_item;
+  return c;
+}
+
+// Whether a wait of this launch has run out (the status word is set).
+__device__ __forceinline__ bool failed(const int* status) {
+  return *reinterpret_cast<const volatile int*>(status) != 0;
+}
+
+// All consumer threads' `v` and-ed (named barrier 1), so every consumer warp
+// takes the same way out of the item loop.
+__device__ __forceinline__ bool consumers_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kThreads)
+      : "memory");
+  return r != 0;
+}
+
+// Whether the 3 x 3 neighbourhood of the item's tile has finished pass s - 1
+// (lanes 0..8 read one pass counter each, acquire).  With `block` it waits
+// until they have (bounded: past the limit, or once another wait of the
+// launch ran out, it records a timeout and returns true; the producer then
+// ends its CTA's queue, see batch_kernel).
+__device__ __forceinline__ bool deps_ready(const BatchJob& jb, const Claim& c, bool block, int lane, int* status,
+                                           long long limit) {
+  bool mine = true;
+  if (c.s > 0 && lane < 9) {
+    const int ntx = c.tx + lane % 3 - 1, nty = c.ty + lane / 3 - 1;
+    if (ntx >= 0 && nty >= 0 && ntx < jb.tiles_x && nty < jb.tiles_y) {
+      const int* flag = jb.done + nty * jb.tiles_x + ntx;
+      if (ld_acquire(flag) < c.s) {
+        if (!block) {
+          mine = false;
+        } else {
+          const long long t0 = clock64();
+          while (ld_acquire(flag) < c.s) {
+            // past the limit, or another wait already ran out: give up
+            if (clock64() - t0 > limit || failed(status)) { atomicExch(status, kStatusTimeout); break; }
+            __nanosleep(128);
+          }
+        }
+      }
+    }
+  }
+  const bool all = __all_sync(0xffffffffu, mine);
+  __syncwarp();  // the other lanes' acquires before lane 0's load below
+  return all;
+}
+
+// Asynchronous global -> shared copy of `bytes` bytes (16-byte aligned, a
+// multiple of 16), completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Where the producer puts an item's data for the consumers.
+struct Stage {
+  float* box;            // the item's input box
+  uint4* ops_a;          // the job's packed A operands (2r + 2 per lane)
+  uint32_t* ops_e;       // its metadata words
+  BatchJob* job;         // its record
+  ItemSlot* slot;
+  uint64_t* full;        // completes when all of it has landed
+};
+
+// Lane 0 hands item `c` to the consumers: its slot, then (completing
+// `full`) its box (TMA) and, when the job differs from the previous item's
+// (`*prev_job`), the job's record and packed operands (bulk copies from
+// `jobs_g`, the job table in global memory, and the plan's buffers); a plain
+// arrival when there is nothing to load (the end, a left-out item).
+// Returns whether a copy was issued.
+__device__ __forceinline__ bool hand_over(const Claim& c, const BatchJob* __restrict__ jobs,
+                                         const BatchJob* __restrict__ jobs_g, const CUtensorMap* __restrict__ maps,
+                                         const Stage& sg, int* prev_job, int lane) {
+  bool copies = false;
+  if (lane == 0) {
+    sg.slot->job = c.job;
+    sg.slot->s = c.s;
+    sg.slot->tile = c.tile;
+    sg.slot->end = c.end;
+    sg.slot->skip = c.skip;
+    const BatchJob* jb = (c.end || c.skip) ? nullptr : &jobs[c.job];
+    if (jb) {
+      // the box, unless the consumers load this first pass themselves
+      const bool box = c.s > 0 || jb->tma0;
+      const bool fresh = c.job != *prev_job;
+      const int np = pass_steps(*jb, c.s);
+      const int bw = jb->bx + 2 * kHaloX * np, bh = jb->by + 2 * jb->r * np;
+      const uint32_t na = 2 * jb->r + 2;
+      const uint32_t bytes = (box ? (uint32_t)(bw * bh * 4) : 0u) +
+                             (fresh ? na * 16 * 32 + na * 4 * 32 + (uint32_t)sizeof(BatchJob) : 0u);
+      if (bytes > 0) {
+        mbar_arrive_expect_tx(sg.full, bytes);
+        if (box) {
+          // the neighbours' generic-proxy stores must be visible to the TMA read
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          // the pass's input box: the tile grown by r rows and 4 columns per step
+          const int src_map = jb->map0 + (np == 1 ? 3 : 0) + (c.s == 0 ? 0 : 1 + (jb->first + c.s - 1) % 2);
+          tma_load_3d(sg.box, &maps[src_map], sg.full, c.tx * jb->bx - kHaloX * np, c.ty * jb->by - jb->r * np, 0);
+        }
+        if (fresh) {
+          bulk_load(sg.ops_a, jb->a, na * 16 * 32, sg.full);
+          bulk_load(sg.ops_e, jb->meta, na * 4 * 32, sg.full);
+          bulk_load(sg.job, jobs_g + c.job, (uint32_t)sizeof(BatchJob), sg.full);
+          *prev_job = c.job;
+        }
+        copies = true;
+      } else {
+        mbar_arrive(sg.full);
+      }
+    } else {
+      mbar_arrive(sg.full);
+    }
+  }
+  return __shfl_sync(0xffffffffu, (int)copies, 0) != 0;
+}
+
+// The persistent queue kernel: seven consumer warps compute the items'
+// tiles; one producer warp claims the items, decodes them, tests their
+// dependencies and loads their boxes, one item ahead of the consumers, so
+// that work runs beside the tensor-core work.  One stage: the next item's
+// box is loaded into it as soon as the consumers have read the current one
+// (after level 1 of a two-step item), so the load overlaps level 2.  Three
+// CTAs per SM, as for the stand-alone fused kernel.
+//
+// The producer never blocks on another CTA's progress while its CTA holds
+// an unpublished item: the next item's dependencies are first only tested;
+// if they are not met, the producer publishes the current item before it
+// waits for them (and claims nothing further meanwhile).  Every awaited item
+// is of an earlier pass, hence claimed earlier, and the earliest unfinished
+// item always progresses: the queue cannot deadlock, whatever the residency.
+// Once any wait of the launch has run out (status word set), every producer
+// stops claiming and every dependency wait gives up at once, so a failure
+// ends the launch promptly instead of draining the queue one expired wait at
+// a time.
+//
+// The queue tables (job records, (job, pass) entries, tile prefix sums) are
+// one contiguous block `tables` of `tables_bytes` bytes whose parts start at
+// the given offsets; with `tables_in_smem` the CTA copies the block into
+// shared memory first.
+__global__ void __launch_bounds__(kQueueThreads, 3) batch_kernel(const unsigned char* __restrict__ tables,
                                                              int tables_bytes, int tables_in_smem, int o_ent,
                                                              int o_prefix, int n_ent,
                                                              const CUtensorMap* __restrict__ maps,
                                                              int* __restrict__ counter, int* __restrict__ status,
-                                                             long long wait_cycles, long long drop_item) {
+                                                             long long wait_cycles, long long drop_item,
+                                                             int claim_ahead) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_u32 = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (base_u32 & 1023)) & 1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kStageStride);
-  uint64_t* empty = full + 2;
-  ItemSlot* slot = reinterpret_cast<ItemSlot*>(empty + 2);
-  volatile long long* claim_turn = reinterpret_cast<volatile long long*>(slot + 2);
-  float* level = reinterpret_cast<float*>(smem + 2 * kStageStride + 128);  // level 1 of two-step items
-  unsigned char* tsm = smem + 2 * kStageStride + 128 + kLevelFloats * 4;
+  float* stage = reinterpret_cast<float*>(smem);
+  float* level = reinterpret_cast<float*>(smem + kLevelOff);  // level 1 of two-step items
+  // full: the item's box (or slot) is ready; boxfree: the consumers have
+  // read the box; done[k & 1]: the consumers have stored item k.  `done`
+  // alternates between two barriers because the consumers may finish item
+  // k + 1 before the producer, busy claiming, has waited for item k: with
+  // one barrier that wait would then see the wrong phase.  (`full` and
+  // `boxfree` cannot run ahead: each completes only after the producer's
+  // previous wait on it.)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint64_t* boxfree = full + 1;
+  uint64_t* done = full + 2;  // two barriers
+  ItemSlot* slot = reinterpret_cast<ItemSlot*>(full + 4);
+  Stage sg;
+  sg.box = stage;
+  sg.ops_a = reinterpret_cast<uint4*>(smem + kOpsOff);
+  sg.ops_e = reinterpret_cast<uint32_t*>(smem + kOpsOff + kOpsABytes);
+  sg.job = reinterpret_cast<BatchJob*>(smem + kJobOff);
+  sg.slot = slot;
+  sg.full = full;
+  const BatchJob* jobs_g = reinterpret_cast<const BatchJob*>(tables);  // the global copy (bulk-copy source)
+  unsigned char* tsm = smem + kTablesOff;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tables_in_smem) {
     const uint4* src = reinterpret_cast<const uint4*>(tables);
@@ -368,126 +542,82 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
   const int2* __restrict__ ent = reinterpret_cast<const int2*>(tb + o_ent);  // (job, pass)
   const long long* __restrict__ ent_prefix = reinterpret_cast<const long long*>(tb + o_prefix);
   if (tid == 0) {
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(&full[k], 1);
-      mbar_init(&empty[k], kThreads / 32);  // one arrival per consumer warp
-    }
-    *claim_turn = 0;
+    mbar_init(full, 1);
+    mbar_init(boxfree, 1);
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
   const long long total = ent_prefix[n_ent];
 
-  if (warp >= kThreads / 32) {
-    // ---------------- producer warps: warp p owns stage p ----------------
-    const int st = warp - kThreads / 32;
-    int pj = -1, ptile = 0, ps = 0;  // the item this stage held last
-    for (long long use = 0;; ++use) {
-      const long long k = 2 * use + st;  // the consumers' index of this item
-      // claim in the consumers' order: item k only after item k - 1.  The
-      // claim and the decode run while the stage still holds item k - 2.
-      long long item = 0;
-      bool ok = true;
-      if (lane == 0) {
-        const long long t0 = clock64();
-        while (*claim_turn != k) {
-          if (clock64() - t0 > wait_cycles) { atomicExch(status, kStatusTimeout); ok = false; break; }
-          __nanosleep(64);
-        }
-        if (ok) {
-          __threadfence_block();  // the other warp's claim before this one
-          item = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ULL);
-          __threadfence_block();
-          *claim_turn = k + 1;
-        }
+  if (warp == kConsumerWarps) {
+    // ---------------- producer warp ----------------
+    // the first item: nothing is held yet, so its dependencies may be awaited
+    int prev_job = -1;  // the job whose record and operands the consumers have (lane 0)
+    Claim cur = claim_item(counter, total, ent_prefix, ent, n_ent, jobs, drop_item, lane);
+    if (!cur.end && !cur.skip) (void)deps_ready(jobs[cur.job], cur, true, lane, status, wait_cycles);
+    bool last_tma = hand_over(cur, jobs, jobs_g, maps, sg, &prev_job, lane);
+    long long handed = 1;  // phases of `full` handed over
+    bool ok = true;
+    // The item after `cur` is claimed, decoded and its dependencies tested
+    // while the consumers compute `cur` (pass counters only grow: a test
+    // passed early still holds when the box is loaded).  With `claim_ahead`
+    // (queues whose layers are much wider than the grid) the claim of the
+    // item after that follows as soon as `nxt` is handed over, i.e. during
+    // the last level of `cur`: the producer's claim, decode and test then
+    // never delay a load.  On narrow queues, whose items wait for their
+    // neighbours, claiming that early only reserves items a CTA cannot start
+    // yet, so there the claim waits for the next item.  After a failed wait
+    // anywhere in the launch (status word set) the producer claims nothing
+    // more: the CTA's queue ends after the items it holds.
+    auto claim_tested = [&](Claim& c) -> bool {
+      if (failed(status)) {
+        c = Claim{};
+        c.end = 1;
+        return true;
       }
+      c = claim_item(counter, total, ent_prefix, ent, n_ent, jobs, drop_item, lane);
+      return c.end || c.skip || deps_ready(jobs[c.job], c, false, lane, status, wait_cycles);
+    };
+    Claim nxt = {};
+    bool have_nxt = false, ready = false;
+    for (long long k = 0; !cur.end; ++k) {
+      const uint32_t par = (uint32_t)(k & 1);
+      if (!have_nxt) ready = claim_tested(nxt);
+      if (lane == 0) ok = mbar_wait_backoff(boxfree, par, status, 32, wait_cycles);
       if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
-      item = __shfl_sync(0xffffffffu, item, 0);
-      const bool end = item >= total;
-      int s = 0, j = 0, tile = 0, tx = 0, ty = 0;
-      if (!end) {
-        const int e = warp_search(ent_prefix, n_ent, item, lane);
-        const int2 je = ent[e];
-        j = je.x;
-        s = je.y;
-        tile = (int)(item - ent_prefix[e]);
-        tx = tile % jobs[j].tiles_x;
-        ty = tile / jobs[j].tiles_x;
-      }
-      // every consumer warp must have handed the stage back (use - 1); its
-      // stores of that item are then ordered before this warp's release of
-      // the item's pass counter (the fence waits here, not in the consumers)
-      if (use > 0) {
-        if (lane == 0) ok = mbar_wait_backoff(&empty[st], (uint32_t)((use - 1) & 1), status, 128, wait_cycles);
-        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
-        if (lane == 0 && pj >= 0) st_release(jobs[pj].done + ptile, ps + 1);
-      }
-      if (end) {
-        if (lane == 0) {
-          slot[st].end = 1;
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
-        }
-        break;
-      }
-      const BatchJob& jb = jobs[j];
-      if (item == drop_item) {
-        // left out on purpose: the consumers skip it and its tile's step
-        // counter stays behind, so the items that need it wait until their
-        // limit runs out
-        pj = -1;
-        __syncwarp();
-        if (lane == 0) {
-          slot[st].job = j;
-          slot[st].s = s;
-          slot[st].tile = tile;
-          slot[st].end = 0;
-          slot[st].skip = 1;
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
-        }
-        __syncwarp();
-        continue;
-      }
-      // lanes 0..8 each wait for one tile of the 3 x 3 neighbourhood (step
-      // s-1); after the release above, so a wait on this CTA's own item k - 2
-      // cannot block its publication
-      if (s > 0 && lane < 9) {
-        const int ntx = tx + lane % 3 - 1, nty = ty + lane / 3 - 1;
-        if (ntx >= 0 && nty >= 0 && ntx < jb.tiles_x && nty < jb.tiles_y) {
-          const int* flag = jb.done + nty * jb.tiles_x + ntx;
-          if (ld_acquire(flag) < s) {
-            const long long t0 = clock64();
-            while (ld_acquire(flag) < s) {
-              if (clock64() - t0 > wait_cycles) { atomicExch(status, kStatusTimeout); break; }
-              __nanosleep(128);
-            }
-          }
+      // item k's box is read: load the next one now if it may start
+      if (!ready) ready = deps_ready(jobs[nxt.job], nxt, false, lane, status, wait_cycles);
+      Claim after = {};
+      bool have_after = false, ready_after = false;
+      if (ready) {
+        last_tma = hand_over(nxt, jobs, jobs_g, maps, sg, &prev_job, lane);
+        ++handed;
+        if (claim_ahead && !nxt.end) {
+          ready_after = claim_tested(after);
+          have_after = true;
         }
       }
-      pj = j;
-      ptile = tile;
-      ps = s;
-      __syncwarp();
-      if (lane == 0) {
-        slot[st].job = j;
-        slot[st].s = s;
-        slot[st].tile = tile;
-        slot[st].end = 0;
-        slot[st].skip = 0;
-        if (s > 0 || jb.tma0) {
-          // the neighbours' generic-proxy stores must be visible to the TMA read
-          asm volatile("fence.proxy.async.global;" ::: "memory");
-          // the pass's input box: the tile grown by r rows and 4 columns per step
-          const int np = pass_steps(jb, s);
-          const int bw = jb.bx + 2 * kHaloX * np, bh = jb.by + 2 * jb.r * np;
-          const int src_map = jb.map0 + ((jb.two && np == 1) ? 3 : 0) + (s == 0 ? 0 : 1 + (jb.first + s - 1) % 2);
-          mbar_arrive_expect_tx(&full[st], (uint32_t)(bw * bh * 4));
-          tma_load_3d(smem + st * kStageStride, &maps[src_map], &full[st], tx * jb.bx - kHaloX * np,
-                      ty * jb.by - jb.r * np, 0);
-        } else {
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
-        }
+      // item k's outputs are stored: publish its tile's pass counter
+      if (lane == 0) ok = mbar_wait_backoff(&done[k & 1], (uint32_t)((k >> 1) & 1), status, 32, wait_cycles);
+      if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+      if (lane == 0 && !cur.skip) st_release(jobs[cur.job].done + cur.tile, cur.s + 1);
+      if (!ready) {
+        // this CTA holds no unpublished item now: wait for the dependencies
+        (void)deps_ready(jobs[nxt.job], nxt, true, lane, status, wait_cycles);
+        last_tma = hand_over(nxt, jobs, jobs_g, maps, sg, &prev_job, lane);
+        ++handed;
       }
-      __syncwarp();
+      cur = nxt;
+      nxt = after;
+      have_nxt = have_after;
+      ready = ready_after;
+    }
+    if (!ok && last_tma && lane == 0) {
+      // giving up: the last load may still land in this CTA's shared
+      // memory; wait for it once more (bounded) before the CTA exits
+      (void)mbar_wait_bounded(full, (uint32_t)((handed - 1) & 1), status, wait_cycles);
     }
     return;
   }
@@ -498,75 +628,66 @@ __global__ void __launch_bounds__(kThreads + 64, 2) batch_kernel(const unsigned 
   uint4 A8[kNA];
   uint32_t E8[kNA];
   int cur_job = -1;
-  for (long long k = 0;; ++k) {
-    const int st = (int)(k & 1);
-    const bool landed = mbar_wait_backoff(&full[st], (uint32_t)((k >> 1) & 1), status, 32, wait_cycles);
-    if (!landed) break;
-    const ItemSlot it = slot[st];
+  for (uint32_t k = 0;; ++k) {
+    const bool landed = mbar_wait_backoff(full, k & 1, status, 32, wait_cycles);
+    if (!consumers_all(landed)) break;
+    const ItemSlot it = *slot;
     if (it.end) break;
     if (it.skip) {
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // every consumer has read the slot
+      if (tid == 0) {
+        mbar_arrive(boxfree);
+        mbar_arrive(&done[k & 1]);
+      }
       continue;
     }
-    const BatchJob& jb = jobs[it.job];
+    // the job's record and operands are in shared memory (the producer
+    // copied them there with the box whenever the job changed); the record
+    // is read here, before the item's first barrier, after which the next
+    // item's copy may overwrite it
+    const BatchJob& jb = *sg.job;
     if (it.job != cur_job) {
       const int na = 2 * jb.r + 2;
 #pragma unroll
       for (int a = 0; a < kNA; ++a)
         if (a < na) {
-          A8[a] = jb.a[(size_t)a * 32 + lane];
-          E8[a] = jb.meta[(size_t)a * 32 + lane];
+          A8[a] = sg.ops_a[a * 32 + lane];
+          E8[a] = sg.ops_e[a * 32 + lane];
         }
       cur_job = it.job;
     }
     const int tx = it.tile % jb.tiles_x, ty = it.tile / jb.tiles_x;
     const int np = pass_steps(jb, it.s);
-    float* Sw = reinterpret_cast<float*>(smem + st * kStageStride);
     if (it.s == 0 && !jb.tma0) {
-      // a first pass of one step (head1 for two-step jobs)
+      // a first pass of one step on a grid TMA cannot describe
       load_box_async(jb.in, jb.nx, jb.ny, 1, (int64_t)tx * jb.bx - kHaloX, (int64_t)ty * jb.by - jb.r, 0,
-                     jb.bx + 2 * kHaloX, jb.by + 2 * jb.r, 1, Sw, warp, kThreads / 32, lane);
+                     jb.bx + 2 * kHaloX, jb.by + 2 * jb.r, 1, stage, warp, kConsumerWarps, lane);
       asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
     }
-    const float* S = Sw;
     const bool last = it.s + 1 == jb.passes;
     float* dst = last ? jb.out : jb.bufs[(jb.first + it.s) % 2];
     const int64_t pitch = last ? jb.nx : jb.pitch;
     const bool out_tf32 = !last;
-    if (jb.two) {
-      const int x0 = tx * jb.bx, y0 = ty * jb.by;
-#define SPIDER_BATCH_FUSED(R)                                                                          \
-  if (np == 2) {                                                                                       \
-    if (it.s == 0) batch_fused<R, 2, true>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);  \
-    else batch_fused<R, 2, false>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);          \
-  } else {                                                                                             \
-    if (it.s == 0) batch_fused<R, 1, true>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);  \
-    else batch_fused<R, 1, false>(jb, A8, E8, S, level, dst, pitch, x0, y0, out_tf32, status);          \
+    const int x0 = tx * jb.bx, y0 = ty * jb.by;
+    uint64_t* stored = &done[k & 1];
+#define SPIDER_BATCH_FUSED(R)                                                                               \
+  if (np == 2) {                                                                                            \
+    if (it.s == 0)                                                                                          \
+      batch_fused<R, 2, true>(jb, A8, E8, stage, level, dst, pitch, x0, y0, out_tf32, status, boxfree, stored);  \
+    else                                                                                                    \
+      batch_fused<R, 2, false>(jb, A8, E8, stage, level, dst, pitch, x0, y0, out_tf32, status, boxfree, stored); \
+  } else {                                                                                                  \
+    if (it.s == 0)                                                                                          \
+      batch_fused<R, 1, true>(jb, A8, E8, stage, level, dst, pitch, x0, y0, out_tf32, status, boxfree, stored);  \
+    else                                                                                                    \
+      batch_fused<R, 1, false>(jb, A8, E8, stage, level, dst, pitch, x0, y0, out_tf32, status, boxfree, stored); \
   }
-      switch (jb.r) {
-        case 1: SPIDER_BATCH_FUSED(1) break;
-        case 2: SPIDER_BATCH_FUSED(2) break;
-        default: SPIDER_BATCH_FUSED(3) break;
-      }
-#undef SPIDER_BATCH_FUSED
-    } else if (it.s == 0) {
-      switch (jb.r) {
-        case 1: batch_tile<1, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-        case 2: batch_tile<2, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-        default: batch_tile<3, true>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-      }
-    } else {
-      switch (jb.r) {
-        case 1: batch_tile<1, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-        case 2: batch_tile<2, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-        default: batch_tile<3, false>(jb, A8, E8, S, dst, pitch, tx * kBX, ty * kBY, out_tf32); break;
-      }
+    switch (jb.r) {
+      case 1: SPIDER_BATCH_FUSED(1) break;
+      case 2: SPIDER_BATCH_FUSED(2) break;
+      default: SPIDER_BATCH_FUSED(3) break;
     }
-    // this warp is done with the stage and has issued its stores; the
-    // producer publishes the tile once all eight warps are here
-    __syncwarp();
-    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+#undef SPIDER_BATCH_FUSED
   }
 }
 
@@ -730,8 +851,8 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       jb.steps = (int)steps[i];
       // two steps per pass on the fused tile for jobs of several steps
       jb.two = (steps[i] > 1 && two_step_items) ? 1 : 0;
-      jb.by = jb.two ? 64 - 2 * p->r : kBY;
-      jb.bx = jb.two ? 120 : kBX;
+      jb.by = kTileL1 - 2 * p->r;  // the queue tile, for one- and two-step passes
+      jb.bx = 120;
       jb.tiles_x = (int)((p->nx + jb.bx - 1) / jb.bx);
       jb.tiles_y = (int)((p->ny + jb.by - 1) / jb.by);
       jb.map0 = 6 * k;
@@ -740,15 +861,14 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       jb.out = outs[i];
       jb.in = ins[i];
       jb.done = nullptr;
-      // boxes: a full pass reads (by + 2r T) x (bx + 8 T) with T = 1 (one-step
-      // tiles) or 2 (fused tiles), both (64 + 2r) x 136; a one-step pass of a
-      // two-step job reads (by + 2r) x (bx + 8) = 64 x 128
-      const int box_x = kBX + 2 * kHaloX, box_y = kBY + 2 * p->r;
-      const int box1_x = 128, box1_y = 64;
+      // boxes: a pass of T steps reads (by + 2r T) x (bx + 8 T): a two-step
+      // pass (56 + 2r) x 136 (maps 0..2), a one-step pass 56 x 128 (maps 3..5)
+      const int box_x = 120 + 4 * kHaloX, box_y = kTileL1 + 2 * p->r;
+      const int box1_x = 128, box1_y = kTileL1;
       CUtensorMap* mp = &maps[6 * k];
       std::memset(mp, 0, 6 * sizeof(CUtensorMap));
       jb.tma0 = make_tensor_map(&mp[0], ins[i], p->nx, p->ny, 1, box_x, box_y, 1) ? 1 : 0;
-      if (jb.tma0 && jb.two) make_tensor_map(&mp[3], ins[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
+      if (jb.tma0) make_tensor_map(&mp[3], ins[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
       if (jb.two) {
         jb.head1 = (jb.steps % 2 == 1 || !jb.tma0) ? 1 : 0;
         jb.tail1 = ((jb.steps - jb.head1) % 2 == 1) ? 1 : 0;
@@ -766,10 +886,8 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
         jb.bufs[0] = outs[i];
         jb.bufs[1] = p->dev.scratch;
         if (jb.passes == 1) mp[2] = mp[0];
-        if (jb.two) {
-          make_tensor_map(&mp[4], outs[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
-          if (jb.passes > 1) make_tensor_map(&mp[5], p->dev.scratch, p->nx, p->ny, 1, box1_x, box1_y, 1);
-        }
+        make_tensor_map(&mp[4], outs[i], p->nx, p->ny, 1, box1_x, box1_y, 1);
+        if (jb.passes > 1) make_tensor_map(&mp[5], p->dev.scratch, p->nx, p->ny, 1, box1_x, box1_y, 1);
       } else {
         jb.pitch = (p->nx + 3) / 4 * 4;
         jb.first = 0;
@@ -782,8 +900,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
           jb.bufs[1] = p->dev.pad + grid_bytes / 4;
           for (int m = 0; m < 2; ++m) {
             if (!make_tensor_map_pitched(&mp[1 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box_x, box_y, 1) ||
-                (jb.two &&
-                 !make_tensor_map_pitched(&mp[4 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box1_x, box1_y, 1)))
+                !make_tensor_map_pitched(&mp[4 + m], jb.bufs[m], p->nx, p->ny, 1, jb.pitch, box1_x, box1_y, 1))
               return fail(SPIDER_ERR_CUDA, "tensor map of a padded grid");
           }
         }
@@ -796,16 +913,19 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     // Queue order: entries (job, pass), each covering the job's tiles, in
     // pass-major order (pass 0 of every job, then pass 1, ...), jobs of more
     // passes first within a pass, so an item only waits for items earlier in
-    // the queue.  (An order that advances every job in proportion to its
-    // pass count -- pass p of P in layer p M / P -- measured 3 % faster with
-    // every grid of the 64-grid mix in the queue but 3-9 % slower on 256
-    // small grids, the queue's default workload.)
+    // the queue.  (Measured alternatives with every grid of the 64-grid mix
+    // in the queue: an order that advances every job in proportion to its
+    // pass count -- pass p of P in layer p M / P -- 3 % faster there but 3-9 %
+    // slower on 256 small grids; a window of jobs whose grids fit a byte
+    // budget, so that a job's passes follow one another while its grids sit
+    // in L2, no faster at 96 MB and 13 % slower at 48 MB.)
     std::vector<int> order(nq);
     for (int k = 0; k < nq; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].passes > jobs[b].passes; });
     std::vector<int> ent;  // job, pass, job, pass, ...
     std::vector<long long> ent_prefix(1, 0);
     long long widest_layer = 1;
+    const long long layer_count = max_steps;
     for (int L = 0; L < max_steps; ++L) {
       long long layer_items = 0;
       for (int k = 0; k < nq && jobs[order[k]].passes > L; ++k) {
@@ -868,10 +988,12 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     std::call_once(attr_once, [] {
       attr_err = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kSmemBase + kMaxTableSmem);
+      if (attr_err == cudaSuccess)  // the stage and the level buffer, not L1, take the shared memory
+        attr_err = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     });
     if (attr_err != cudaSuccess) return fail(SPIDER_ERR_CUDA, "batch kernel attributes");
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads + 64, smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kQueueThreads, smem_bytes);
     // No more CTAs than the largest layer has items: further CTAs would
     // mostly wait for earlier passes, holding SMs (and their shared memory)
     // that the fused passes on the side streams can use.
@@ -889,9 +1011,15 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
     int* a_status = reinterpret_cast<int*>(dev + o_status);
     long long a_wait = wait_limit_cycles();
     long long a_drop = drop_item;
+    // claim one item further ahead when the layers are much wider than the
+    // grid (measured: 64-grid mix entirely in the queue 867 -> 957
+    // GStencil/s, one 8192^2 radius-1 grid 1098 -> 1233; on 256 small grids,
+    // whose layers are about as wide as the grid, 282 -> 234)
+    const long long layers = std::max<long long>(1, layer_count);
+    int a_ahead = total_items >= 8LL * grid * layers ? 1 : 0;
     void* kargs[] = {(void*)&a_tables, (void*)&a_tbytes, (void*)&a_tsm, (void*)&a_oe, (void*)&a_op, (void*)&a_ne,
                      (void*)&a_maps, (void*)&a_ctr, (void*)&a_status,
-                     (void*)&a_wait, (void*)&a_drop};
+                     (void*)&a_wait, (void*)&a_drop, (void*)&a_ahead};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphCreate(&graph, 0);
@@ -910,7 +1038,7 @@ extern "C" spider_status spider_batch(int n, const spider_plan* plans, const flo
       cudaKernelNodeParams kp = {};
       kp.func = reinterpret_cast<void*>(batch_kernel);
       kp.gridDim = dim3(grid);
-      kp.blockDim = dim3(kThreads + 64);
+      kp.blockDim = dim3(kQueueThreads);
       kp.sharedMemBytes = smem_bytes;
       kp.kernelParams = kargs;
       e = cudaGraphAddKernelNode(&kern, graph, &reset, 1, &kp);
