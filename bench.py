@@ -647,18 +647,31 @@ def batched_summary(spider, dev, stream, calls=5):
         outs.append(torch.empty_like(ins[-1]))
         work += int(np.prod(jb.extents)) * jb.steps
     steps = [jb.steps for jb in jobs]
-    for _ in range(3):
-        spider.batch(plans, ins, outs, steps, stream)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(calls):
-        spider.batch(plans, ins, outs, steps, stream)
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t0
+
+    def timed():
+        for _ in range(3):
+            spider.batch(plans, ins, outs, steps, stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            spider.batch(plans, ins, outs, steps, stream)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0
+
+    dt = timed()
+    # the same call with every grid in the persistent queue (one launch)
+    spider.batch_configure(1 << 40, 2)
+    try:
+        dt_queue = timed()
+    finally:
+        spider.batch_configure(0, 0)
     for p in plans:
         p.close()
     return {"workload": "batched: 64 2-D grids, sides log-uniform [256, 4096], star/box r 1-3, 10-200 steps",
             "gstencil_s": work * calls / dt / 1e9, "ms_per_call": dt / calls * 1e3, "stencil_updates": work,
+            "launch": "grids of >= 2^16 points as fused passes on side streams, smaller ones in the persistent queue",
+            "queue_only": {"gstencil_s": work * calls / dt_queue / 1e9, "ms_per_call": dt_queue / calls * 1e3,
+                           "launch": "every grid in the persistent tile queue: one kernel launch (a CUDA graph)"},
             "timing": "host clock around synchronous spider_batch calls"}
 
 
@@ -694,6 +707,19 @@ def run_batched(a):
         spider.batch(plans, ins, outs, steps, stream)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
+    # the same calls with every grid in the persistent queue (one launch)
+    spider.batch_configure(1 << 40, 2)
+    try:
+        for _ in range(3):
+            spider.batch(plans, ins, outs, steps, stream)
+        torch.cuda.synchronize(dev)
+        tq = time.perf_counter()
+        for _ in range(a.steps):
+            spider.batch(plans, ins, outs, steps, stream)
+        torch.cuda.synchronize(dev)
+        dt_queue = time.perf_counter() - tq
+    finally:
+        spider.batch_configure(0, 0)
     # the same jobs one after another through spider_run (each plan tuned)
     for p, x, y, n in zip(plans, ins, outs, steps):
         p.autotune(x, y, n, stream)
@@ -716,6 +742,8 @@ def run_batched(a):
                        "launch": "one spider_batch call: grids of >= 2^16 points as fused passes on side streams, "
                                  "each replayed as a CUDA graph; smaller grids and single steps in the persistent "
                                  "tile queue (one graph launch)"},
+            "queue_only": {"value": world * work * a.steps / dt_queue / 1e9, "unit": "GStencil/s",
+                           "launch": "every grid in the persistent tile queue: one kernel launch (a CUDA graph)"},
             "sequential_spider_run": {"value": work / dt_seq / 1e9, "unit": "GStencil/s",
                                       "note": "same jobs, one autotuned spider_run after another"}}
     for p in plans:
